@@ -1,0 +1,208 @@
+/*
+ * lbm.h -- C ABI of the GB300 free-energy D3Q27 lattice Boltzmann library.
+ *
+ * The library advances the chemical-potential-based free-energy LB model with
+ * generalized (sixth-order Hermite) equilibria and central-moment collision of
+ * Saito, Baba & Takada, "A thermodynamically consistent free-energy lattice
+ * Boltzmann model" (arXiv 2504.03819), one time step per call of the hot path.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lattice units, delta_t = c = 1, c_s^2 = 1/3 (Sec. II B).
+ *  - Grid of nx * ny * nz nodes, periodic in x, y and z.  Node index
+ *    n = x + nx * (y + ny * z) (x fastest).  Walls are nodes of the solid mask.
+ *  - Field arrays are structure-of-arrays: a scalar field is N = nx*ny*nz
+ *    floats; a vector field is 3*N floats, component a at offset a*N.
+ *  - Population q (0..26) has velocity c_q = (q%3 - 1, (q/3)%3 - 1, q/9 - 1);
+ *    q = 13 is the rest population and 26 - q is the opposite of q.
+ *    Population arrays are 27*N elements, population q at offset q*N.
+ *  - Memory: the caller owns every buffer.  Device pointers are plain CUDA
+ *    device addresses on the current device; host pointers are ordinary host
+ *    memory.  The library never allocates device memory: all of its device
+ *    state lives in the caller's workspace, and the context keeps views of it
+ *    (and of the solid mask) until lbm_destroy.
+ *  - Streams: all device work of a context is enqueued on the stream given at
+ *    lbm_init_domain (NULL = legacy default stream).  Entry points return after
+ *    enqueueing unless documented otherwise.
+ *  - Errors: every function returning int returns LBM_OK (0) or a negative
+ *    LBM_ERR_* code and never aborts, throws or traps on the device.  Arguments
+ *    are validated before any launch; lbm_last_error gives a message.
+ *  - Arithmetic: FP32 on the device with IEEE division and logf (no fast
+ *    math); FP64 only in the mass / energy reductions.
+ *
+ * Equation numbers follow the paper's numbered displays in order.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,        /* invalid argument (value, size, null pointer) */
+  LBM_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  LBM_ERR_STATE = -3,      /* call out of order (no params / no state yet) */
+  LBM_ERR_NONFINITE = -4,  /* a NaN/Inf density or momentum was detected */
+  LBM_ERR_DOMAIN = -5,     /* a fluid density left (0, 1/b), the EOS domain */
+  LBM_ERR_SIZE = -6        /* workspace too small or grid too large */
+};
+
+/* Population storage type.  Compute is always FP32. */
+enum { LBM_F32 = 0, LBM_F16 = 1 };
+
+/* Wetting modes of the improved wetting boundary (Sec. III C, Eq. 38). */
+enum { LBM_WET_NEUTRAL = 0, LBM_WET_PHI = 1, LBM_WET_DELTA = 2 };
+
+typedef struct lbm_ctx lbm_ctx;
+
+/*
+ * Model parameters.
+ *  a, b, R, T   van der Waals EOS p0 = rho R T/(1 - b rho) - a rho^2 (Eq. 29)
+ *               and its chemical potential (Eq. 32); T is absolute.
+ *               Requires a >= 0, b > 0, R > 0, T > 0.
+ *  kappa        interfacial coefficient of mu = mu0 - kappa lap(rho) (Eq. 2),
+ *               kappa >= 0.
+ *  omega[11]    relaxation rates omega_0..omega_10 of Eqs. 21-26, each in
+ *               [0, 2].
+ *  nu           if > 0, omega_1 is set per node from 1/omega_1 =
+ *               rho nu / p_m + 1/2 (Sec. II B) and omega[1] is ignored.
+ *  q4_correction 1 applies the fourth-order correction of Eq. 28, 0 omits it.
+ *  wetting_mode LBM_WET_NEUTRAL: rho_s = rho_ave;  LBM_WET_PHI: rho_s =
+ *               phi * rho_ave;  LBM_WET_DELTA: rho_s = rho_ave - delta_rho,
+ *               inside the contact-line band and limited to it (Eqs. 37-38).
+ *  wetting_value phi (> 0) or delta_rho (>= 0); ignored when neutral.
+ *  rho_l, rho_v liquid / vapour densities that define the contact-line band
+ *               [0.05 rho_l + 0.95 rho_v, 0.95 rho_l + 0.05 rho_v]; needed
+ *               (rho_l > rho_v > 0) only for the non-neutral modes.
+ *  rho_shift    rho_0 of the stored populations f_i - w_i rho_0.
+ *  check_interval  unused by the step (the non-finite / domain check runs in
+ *               every step at no extra cost); kept for forward compatibility,
+ *               must be >= 0.
+ */
+typedef struct {
+  double a, b, R, T;
+  double kappa;
+  double omega[11];
+  double nu;
+  int q4_correction;
+  int wetting_mode;
+  double wetting_value;
+  double rho_l, rho_v;
+  double rho_shift;
+  int check_interval;
+} lbm_params;
+
+/* Device workspace (bytes) a domain of this size and storage type needs.
+ * Pure host function.  Returns 0 for invalid sizes. */
+size_t lbm_workspace_bytes(int nx, int ny, int nz, int storage);
+
+/*
+ * Create a context for an nx*ny*nz periodic domain (each >= 1, N < 2^31).
+ *  storage       LBM_F32 or LBM_F16 (populations stored as f_i - w_i rho_0).
+ *  solid_mask    device array of N bytes, nonzero = solid node, or NULL for
+ *                an all-fluid domain.  Halfway bounce-back (Sec. III C) acts
+ *                on fluid-solid links; solid nodes next to fluid get rho, mu
+ *                from the wetting scheme (Eqs. 36-38).  Read at init (to list
+ *                boundary nodes) and at every step; must stay valid and
+ *                unchanged until lbm_destroy.
+ *  workspace     device buffer of at least lbm_workspace_bytes(...) bytes,
+ *                256-byte aligned; owned by the caller.
+ *  cuda_stream   cudaStream_t to enqueue on (NULL = default stream).
+ * Synchronises the stream once (to count boundary nodes).  *out is set only
+ * on success.
+ */
+int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage,
+                    const uint8_t *solid_mask, void *workspace, size_t ws_bytes,
+                    void *cuda_stream);
+
+/* Validate and store the model parameters (host struct, copied). */
+int lbm_set_params(lbm_ctx *ctx, const lbm_params *params);
+
+/*
+ * Initial state: populations at the equilibrium whose central moments are
+ * those of Eq. 20 about u0, with rho = rho0 and p_m = (1 + mu(rho0))/3
+ * (mu from Eqs. 2, 32 and the wetting values of Eqs. 36-38 on solid nodes).
+ *  rho0  device, N floats (values on solid nodes are ignored).
+ *  u0    device, 3*N floats SoA, or NULL for u0 = 0.
+ * Requires lbm_set_params.
+ */
+int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0);
+
+/*
+ * Advance n >= 0 time steps (Sec. II B): moments (Eq. 11), wetting density
+ * (Eqs. 37-38), chemical potential (Eqs. 2, 32), wetting chemical potential
+ * (Eq. 36), force (Eq. 12), corrections (Eqs. 27-28), central-moment
+ * collision (Eqs. 19-26) and streaming (Eq. 10) with halfway bounce-back.
+ * Enqueues only; a density that is non-finite or outside (0, 1/b) at the
+ * start of any step sets a status flag read by lbm_sync_status.
+ */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/* Synchronise the context's stream and return LBM_OK, LBM_ERR_NONFINITE or
+ * LBM_ERR_DOMAIN from the device status word (the flags stay set until
+ * lbm_set_state / lbm_set_raw_state / lbm_set_populations). */
+int lbm_sync_status(lbm_ctx *ctx);
+
+/*
+ * Macroscopic fields of the current state (Eq. 11 and Eq. 2): rho (N floats,
+ * wetting value on solid nodes next to fluid), u (3*N floats, force-corrected
+ * velocity, 0 on solid nodes), mu (N floats) and mass_energy (2 doubles:
+ * sum of fluid rho and 1/2 sum of fluid rho |u|^2, FP64 reductions with a
+ * fixed summation order).  All pointers are device pointers and each may be
+ * NULL.
+ */
+int lbm_moments(lbm_ctx *ctx, float *rho, float *u, float *mu, double *mass_energy);
+
+/* Raw state copy: 27*N elements of the storage type (shifted populations),
+ * device to device.  Bitwise round trip. */
+int lbm_get_state(lbm_ctx *ctx, void *f);
+int lbm_set_raw_state(lbm_ctx *ctx, const void *f);
+
+/* Unshifted FP32 populations f_i (27*N floats, device), zero on solid nodes;
+ * and the inverse (stored shifted and rounded to the storage type). */
+int lbm_get_populations(lbm_ctx *ctx, float *f);
+int lbm_set_populations(lbm_ctx *ctx, const float *f);
+
+/* Message for the last error on this context (never NULL). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Free the host-side context (no device memory is owned). */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Number of kernels this context has launched since init. */
+long long lbm_launch_count(const lbm_ctx *ctx);
+
+/* Enable (1) / disable (0) per-kernel CUDA-event timing of lbm_step launches
+ * on the context's stream; enabling clears the accumulators. */
+int lbm_profile_enable(lbm_ctx *ctx, int on);
+
+/* Accumulated device time (ms) and launch count of kernel `id` (0-based, see
+ * lbm_kernel_name) over the profiled lbm_step calls.  Synchronises the
+ * stream.  Returns LBM_ERR_ARG for an unknown id. */
+int lbm_profile_read(lbm_ctx *ctx, int id, double *total_ms, long long *launches);
+
+/* Name of kernel `id` of the step, or NULL past the last one. */
+const char *lbm_kernel_name(int id);
+
+/* ---- host helpers ------------------------------------------------------- */
+
+/*
+ * Coexistence densities of the van der Waals EOS (Eq. 29) at temperature T
+ * below T_c = 8a/(27 R b) (Eq. 30) from Maxwell's equal-area rule (Sec. III):
+ * mu0(rho_l) = mu0(rho_v) and p0(rho_l) = p0(rho_v).  Pure host function.
+ * Returns LBM_ERR_ARG if T >= T_c or a parameter is out of range.
+ */
+int lbm_maxwell(double a, double b, double R, double T, double *rho_l, double *rho_v);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */
