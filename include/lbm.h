@@ -55,6 +55,9 @@ enum {
 /* Population storage type.  Compute is always FP32. */
 enum { LBM_F32 = 0, LBM_F16 = 1 };
 
+/* How stored populations are shifted (see lbm_params.shift_mode). */
+enum { LBM_SHIFT_CONST = 0, LBM_SHIFT_REST = 1 };
+
 /* Wetting modes of the improved wetting boundary (Sec. III C, Eq. 38). */
 enum { LBM_WET_NEUTRAL = 0, LBM_WET_PHI = 1, LBM_WET_DELTA = 2 };
 
@@ -79,7 +82,14 @@ typedef struct lbm_ctx lbm_ctx;
  *  rho_l, rho_v liquid / vapour densities that define the contact-line band
  *               [0.05 rho_l + 0.95 rho_v, 0.95 rho_l + 0.05 rho_v]; needed
  *               (rho_l > rho_v > 0) only for the non-neutral modes.
- *  rho_shift    rho_0 of the stored populations f_i - w_i rho_0.
+ *  shift_mode   LBM_SHIFT_CONST: populations are stored as f_i - w_i rho_0
+ *               with rho_0 = rho_shift.  LBM_SHIFT_REST: f_i(x) is stored
+ *               minus the rest equilibrium of x at the previous step,
+ *               w_i rho + (p_m - rho/3) E_i with E_i the isotropic operator of
+ *               Eq. 16 at u = 0 (-19/9, 2/9, 1/18, 1/72 by speed class); the
+ *               shift bases (rho, p_m - rho/3) are part of the raw state.
+ *               Keeps FP16 storage accurate in dense liquid.
+ *  rho_shift    rho_0 of LBM_SHIFT_CONST.
  *  check_interval  unused by the step (the non-finite / domain check runs in
  *               every step at no extra cost); kept for forward compatibility,
  *               must be >= 0.
@@ -94,6 +104,7 @@ typedef struct {
   double wetting_value;
   double rho_l, rho_v;
   double rho_shift;
+  int shift_mode;
   int check_interval;
 } lbm_params;
 
@@ -158,8 +169,15 @@ int lbm_sync_status(lbm_ctx *ctx);
  */
 int lbm_moments(lbm_ctx *ctx, float *rho, float *u, float *mu, double *mass_energy);
 
-/* Raw state copy: 27*N elements of the storage type (shifted populations),
- * device to device.  Bitwise round trip. */
+/* Bytes of the raw state: 27*N elements of the storage type (shifted
+ * populations, population q at offset q*N) followed, in LBM_SHIFT_REST mode,
+ * by 2*N floats of shift bases.  Depends on the parameters (call after
+ * lbm_set_params); 0 on error. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+
+/* Raw state copy (lbm_state_bytes bytes), device to device.  Bitwise round
+ * trip: lbm_set_raw_state of a saved state reproduces the same trajectory.
+ * Population slots of solid nodes are never read. */
 int lbm_get_state(lbm_ctx *ctx, void *f);
 int lbm_set_raw_state(lbm_ctx *ctx, const void *f);
 

@@ -1,0 +1,427 @@
+// C ABI of the library (include/lbm.h): argument validation, workspace
+// layout, context state and the host-side Maxwell construction.  Every device
+// operation is a kernel from lbm_forward.cu enqueued on the context stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+// Workspace layout (each region 256-byte aligned):
+//   f[0], f[1]      27 N elements of the storage type each
+//   fields          rho N, j 3N, mu N, u 3N, F 3N, phi 3N, Q 3N, sb 2N floats
+//   boundary list   N ints
+//   reduction       RED_BLOCKS * 2 doubles
+//   status          2 ints
+struct Layout {
+  size_t f0, f1, fields, bnd, red, status, total;
+};
+
+bool layout(int nx, int ny, int nz, int storage, Layout *L) {
+  if (nx < 1 || ny < 1 || nz < 1) return false;
+  if (storage != LBM_F32 && storage != LBM_F16) return false;
+  long long N = (long long)nx * ny * nz;
+  if (N >= (1LL << 31)) return false;
+  size_t elem = storage == LBM_F16 ? 2 : 4;
+  size_t off = 0;
+  L->f0 = off; off = align_up(off + 27 * (size_t)N * elem);
+  L->f1 = off; off = align_up(off + 27 * (size_t)N * elem);
+  L->fields = off; off = align_up(off + 19 * (size_t)N * sizeof(float));
+  L->bnd = off; off = align_up(off + (size_t)N * sizeof(int));
+  L->red = off; off = align_up(off + (size_t)RED_BLOCKS * 2 * sizeof(double));
+  L->status = off; off = align_up(off + 2 * sizeof(int));
+  L->total = off;
+  return true;
+}
+
+int fail(lbm_ctx *ctx, int code, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int check_cuda(lbm_ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+int validate(lbm_ctx *ctx, const lbm_params *p) {
+  if (!p) return fail(ctx, LBM_ERR_ARG, "params is NULL");
+  if (!finite(p->a) || p->a < 0) return fail(ctx, LBM_ERR_ARG, "a must be finite and >= 0");
+  if (!finite(p->b) || p->b <= 0) return fail(ctx, LBM_ERR_ARG, "b must be > 0");
+  if (!finite(p->R) || p->R <= 0) return fail(ctx, LBM_ERR_ARG, "R must be > 0");
+  if (!finite(p->T) || p->T <= 0) return fail(ctx, LBM_ERR_ARG, "T must be > 0");
+  if (!finite(p->kappa) || p->kappa < 0) return fail(ctx, LBM_ERR_ARG, "kappa must be >= 0");
+  for (int i = 0; i < 11; ++i)
+    if (!finite(p->omega[i]) || p->omega[i] < 0 || p->omega[i] > 2)
+      return fail(ctx, LBM_ERR_ARG, "omega[%d] must lie in [0, 2]", i);
+  if (!finite(p->nu) || p->nu < 0) return fail(ctx, LBM_ERR_ARG, "nu must be >= 0");
+  if (p->q4_correction != 0 && p->q4_correction != 1) return fail(ctx, LBM_ERR_ARG, "q4_correction must be 0 or 1");
+  if (p->wetting_mode < LBM_WET_NEUTRAL || p->wetting_mode > LBM_WET_DELTA)
+    return fail(ctx, LBM_ERR_ARG, "unknown wetting_mode %d", p->wetting_mode);
+  if (p->wetting_mode != LBM_WET_NEUTRAL) {
+    if (!finite(p->wetting_value) || (p->wetting_mode == LBM_WET_PHI ? p->wetting_value <= 0 : p->wetting_value < 0))
+      return fail(ctx, LBM_ERR_ARG, "wetting_value out of range for the wetting mode");
+    if (!finite(p->rho_l) || !finite(p->rho_v) || !(p->rho_l > p->rho_v && p->rho_v > 0))
+      return fail(ctx, LBM_ERR_ARG, "wetting needs rho_l > rho_v > 0");
+  }
+  if (!finite(p->rho_shift)) return fail(ctx, LBM_ERR_ARG, "rho_shift must be finite");
+  if (p->shift_mode != LBM_SHIFT_CONST && p->shift_mode != LBM_SHIFT_REST)
+    return fail(ctx, LBM_ERR_ARG, "unknown shift_mode %d", p->shift_mode);
+  if (p->check_interval < 0) return fail(ctx, LBM_ERR_ARG, "check_interval must be >= 0");
+  return LBM_OK;
+}
+
+void harvest_profile(lbm_ctx *ctx) {
+  for (auto &e : ctx->prof_pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e.start, e.stop) == cudaSuccess) {
+      ctx->prof_ms[e.id] += ms;
+      ctx->prof_n[e.id] += 1;
+    }
+    ctx->prof_free.push_back(e.start);
+    ctx->prof_free.push_back(e.stop);
+  }
+  ctx->prof_pending.clear();
+  cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_maxwell(double a, double b, double R, double T, double *rho_l, double *rho_v);
+
+size_t lbm_workspace_bytes(int nx, int ny, int nz, int storage) {
+  Layout L;
+  return layout(nx, ny, nz, storage, &L) ? L.total : 0;
+}
+
+int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const uint8_t *solid_mask,
+                    void *workspace, size_t ws_bytes, void *cuda_stream) {
+  if (!out) return LBM_ERR_ARG;
+  Layout L;
+  if (nx < 1 || ny < 1 || nz < 1 || (storage != LBM_F32 && storage != LBM_F16)) return LBM_ERR_ARG;
+  if (!layout(nx, ny, nz, storage, &L)) return LBM_ERR_SIZE;
+  if (!workspace || ((uintptr_t)workspace % ALIGN) != 0) return LBM_ERR_ARG;
+  if (ws_bytes < L.total) return LBM_ERR_SIZE;
+  lbm_ctx *ctx = new (std::nothrow) lbm_ctx();
+  if (!ctx) return LBM_ERR_ARG;
+  ctx->nx = nx;
+  ctx->ny = ny;
+  ctx->nz = nz;
+  ctx->N = nx * ny * nz;
+  ctx->storage = storage;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->mask = solid_mask;
+  char *base = (char *)workspace;
+  ctx->f[0] = base + L.f0;
+  ctx->f[1] = base + L.f1;
+  ctx->cur = 0;
+  float *fl = (float *)(base + L.fields);
+  size_t N = ctx->N;
+  ctx->fld.rho = fl;
+  ctx->fld.j = fl + N;
+  ctx->fld.mu = fl + 4 * N;
+  ctx->fld.u = fl + 5 * N;
+  ctx->fld.F = fl + 8 * N;
+  ctx->fld.phi = fl + 11 * N;
+  ctx->fld.Q = fl + 14 * N;
+  ctx->fld.sb = fl + 17 * N;
+  ctx->bnd = (int *)(base + L.bnd);
+  ctx->red_partial = (double *)(base + L.red);
+  ctx->status = (int *)(base + L.status);
+  ctx->kp.nx = nx;
+  ctx->kp.ny = ny;
+  ctx->kp.nz = nz;
+  ctx->kp.N = ctx->N;
+  cudaGetLastError();
+  cudaMemsetAsync(ctx->fld.rho, 0, 19 * N * sizeof(float), ctx->stream);
+  // solid-node population slots are never written by the step: start them at 0
+  cudaMemsetAsync(ctx->f[0], 0, L.f1 - L.f0, ctx->stream);
+  cudaMemsetAsync(ctx->f[1], 0, L.f1 - L.f0, ctx->stream);
+  cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), ctx->stream);
+  ctx->n_bnd = 0;
+  if (solid_mask) {
+    launch_mark_boundary(ctx);
+    int cnt = 0;
+    cudaMemcpyAsync(&cnt, ctx->status + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+      int rc = check_cuda(ctx, "boundary list");
+      delete ctx;
+      return rc == LBM_OK ? LBM_ERR_CUDA : rc;
+    }
+    ctx->n_bnd = cnt;
+  }
+  if (check_cuda(ctx, "lbm_init_domain") != LBM_OK) {
+    delete ctx;
+    return LBM_ERR_CUDA;
+  }
+  *out = ctx;
+  return LBM_OK;
+}
+
+int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
+  if (!ctx) return LBM_ERR_ARG;
+  int rc = validate(ctx, p);
+  if (rc != LBM_OK) return rc;
+  ctx->params = *p;
+  KParams &k = ctx->kp;
+  k.RT = (float)(p->R * p->T);
+  k.a = (float)p->a;
+  k.b = (float)p->b;
+  k.kappa = (float)p->kappa;
+  for (int i = 0; i < 11; ++i) k.om[i] = (float)p->omega[i];
+  k.nu = (float)p->nu;
+  k.q4 = p->q4_correction;
+  k.rho_shift = (float)p->rho_shift;
+  k.shift_mode = p->shift_mode;
+  k.wet_mode = p->wetting_mode;
+  k.wet_value = (float)p->wetting_value;
+  k.band_lo = (float)(0.05 * p->rho_l + 0.95 * p->rho_v);
+  k.band_hi = (float)(0.95 * p->rho_l + 0.05 * p->rho_v);
+  // references of the mu' = mu - mu_ref form: the coexistence densities below
+  // T_c (where mu0(rho_l) = mu0(rho_v) = mu_ref), the critical density above
+  double rl = 1.0 / (3.0 * p->b), rv = rl;
+  if (!(p->a > 0 && p->T < 8.0 * p->a / (27.0 * p->R * p->b) &&
+        lbm_maxwell(p->a, p->b, p->R, p->T, &rl, &rv) == LBM_OK)) {
+    rl = rv = 1.0 / (3.0 * p->b);
+  }
+  const double RT = p->R * p->T;
+  auto mu0 = [&](double r) {
+    return RT * (std::log(r / (1 - p->b * r)) + 1 / (1 - p->b * r)) - 2 * p->a * r;
+  };
+  const double mu_ref = 0.5 * (mu0(rl) + mu0(rv));
+  k.mu_ref = (float)mu_ref;
+  k.pm_ref = (float)((1.0 + mu_ref) / 3.0);
+  k.rho_split = (float)(0.5 * (rl + rv));
+  const double refs[2] = {rv, rl};
+  for (int i = 0; i < 2; ++i) {
+    k.ref_rho[i] = (float)refs[i];
+    k.ref_omb[i] = (float)(1.0 - p->b * (double)(float)refs[i]);
+    k.ref_dmu[i] = (float)(mu0((double)(float)refs[i]) - mu_ref);
+  }
+  ctx->have_params = 1;
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->have_params) return fail(ctx, LBM_ERR_STATE, "lbm_set_params must come first");
+  if (!rho0) return fail(ctx, LBM_ERR_ARG, "rho0 is NULL");
+  cudaGetLastError();
+  cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+  launch_init(ctx, rho0, u0);
+  int rc = check_cuda(ctx, "lbm_set_state");
+  if (rc == LBM_OK) ctx->have_state = 1;
+  return rc;
+}
+
+int lbm_step(lbm_ctx *ctx, int n) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+  if (!ctx->have_state) return fail(ctx, LBM_ERR_STATE, "no state: call lbm_set_state first");
+  cudaGetLastError();
+  for (int i = 0; i < n; ++i) launch_step(ctx);
+  return check_cuda(ctx, "lbm_step");
+}
+
+int lbm_sync_status(lbm_ctx *ctx) {
+  if (!ctx) return LBM_ERR_ARG;
+  int st = 0;
+  cudaGetLastError();
+  cudaMemcpyAsync(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return check_cuda(ctx, "lbm_sync_status");
+  if (st & STATUS_NONFINITE) return fail(ctx, LBM_ERR_NONFINITE, "non-finite density or momentum");
+  if (st & STATUS_DOMAIN) return fail(ctx, LBM_ERR_DOMAIN, "density outside (0, 1/b)");
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *ctx, float *rho, float *u, float *mu, double *mass_energy) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->have_state) return fail(ctx, LBM_ERR_STATE, "no state");
+  cudaGetLastError();
+  const bool need_u = u || mass_energy;
+  launch_fields(ctx, need_u);
+  size_t N = ctx->N;
+  if (rho) cudaMemcpyAsync(rho, ctx->fld.rho, N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (mu) launch_copy_mu(ctx, mu);
+  if (u) cudaMemcpyAsync(u, ctx->fld.u, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (mass_energy) launch_reduce(ctx, mass_energy);
+  return check_cuda(ctx, "lbm_moments");
+}
+
+size_t lbm_state_bytes(const lbm_ctx *ctx) {
+  if (!ctx || !ctx->have_params) return 0;
+  size_t pops = 27 * (size_t)ctx->N * (ctx->storage == LBM_F16 ? 2 : 4);
+  return pops + (ctx->kp.shift_mode == LBM_SHIFT_REST ? 2 * (size_t)ctx->N * sizeof(float) : 0);
+}
+
+int lbm_get_state(lbm_ctx *ctx, void *f) {
+  if (!ctx || !f) return LBM_ERR_ARG;
+  if (!ctx->have_state) return fail(ctx, LBM_ERR_STATE, "no state");
+  size_t pops = 27 * (size_t)ctx->N * (ctx->storage == LBM_F16 ? 2 : 4);
+  cudaGetLastError();
+  cudaMemcpyAsync(f, ctx->f[ctx->cur], pops, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (ctx->kp.shift_mode == LBM_SHIFT_REST)
+    cudaMemcpyAsync((char *)f + pops, ctx->fld.sb, 2 * (size_t)ctx->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                    ctx->stream);
+  return check_cuda(ctx, "lbm_get_state");
+}
+
+int lbm_set_raw_state(lbm_ctx *ctx, const void *f) {
+  if (!ctx || !f) return LBM_ERR_ARG;
+  if (!ctx->have_params) return fail(ctx, LBM_ERR_STATE, "lbm_set_params must come first");
+  size_t pops = 27 * (size_t)ctx->N * (ctx->storage == LBM_F16 ? 2 : 4);
+  cudaGetLastError();
+  cudaMemcpyAsync(ctx->f[ctx->cur], f, pops, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (ctx->kp.shift_mode == LBM_SHIFT_REST)
+    cudaMemcpyAsync(ctx->fld.sb, (const char *)f + pops, 2 * (size_t)ctx->N * sizeof(float),
+                    cudaMemcpyDeviceToDevice, ctx->stream);
+  cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+  int rc = check_cuda(ctx, "lbm_set_raw_state");
+  if (rc == LBM_OK) ctx->have_state = 1;
+  return rc;
+}
+
+int lbm_get_populations(lbm_ctx *ctx, float *f) {
+  if (!ctx || !f) return LBM_ERR_ARG;
+  if (!ctx->have_state) return fail(ctx, LBM_ERR_STATE, "no state");
+  cudaGetLastError();
+  launch_get_populations(ctx, f);
+  return check_cuda(ctx, "lbm_get_populations");
+}
+
+int lbm_set_populations(lbm_ctx *ctx, const float *f) {
+  if (!ctx || !f) return LBM_ERR_ARG;
+  if (!ctx->have_params) return fail(ctx, LBM_ERR_STATE, "lbm_set_params must come first");
+  cudaGetLastError();
+  launch_set_populations(ctx, f);
+  cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+  int rc = check_cuda(ctx, "lbm_set_populations");
+  if (rc == LBM_OK) ctx->have_state = 1;
+  return rc;
+}
+
+const char *lbm_last_error(const lbm_ctx *ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void lbm_destroy(lbm_ctx *ctx) {
+  if (!ctx) return;
+  if (!ctx->prof_pending.empty()) {
+    cudaStreamSynchronize(ctx->stream);
+    harvest_profile(ctx);
+  }
+  for (cudaEvent_t e : ctx->prof_free) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete ctx;
+}
+
+long long lbm_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int lbm_profile_enable(lbm_ctx *ctx, int on) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (on) {
+    if (!ctx->prof_pending.empty()) {
+      cudaStreamSynchronize(ctx->stream);
+      harvest_profile(ctx);
+    }
+    for (int i = 0; i < K_COUNT; ++i) {
+      ctx->prof_ms[i] = 0.0;
+      ctx->prof_n[i] = 0;
+    }
+  }
+  ctx->prof_on = on ? 1 : 0;
+  return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx *ctx, int id, double *total_ms, long long *launches) {
+  if (!ctx || id < 0 || id >= K_COUNT) return LBM_ERR_ARG;
+  if (!ctx->prof_pending.empty()) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return check_cuda(ctx, "lbm_profile_read");
+    harvest_profile(ctx);
+  }
+  if (total_ms) *total_ms = ctx->prof_ms[id];
+  if (launches) *launches = ctx->prof_n[id];
+  return LBM_OK;
+}
+
+const char *lbm_kernel_name(int id) { return kernel_name(id); }
+
+}  // extern "C"
+
+// Maxwell equal-area construction for the vdW EOS (Sec. III, Eqs. 29-32):
+// find the coexistence pressure by bisection between the spinodal pressures;
+// at each trial pressure the outer roots of p0(rho) = p are the two phases and
+// mu0(rho_l) - mu0(rho_v) changes sign at coexistence.
+namespace {
+struct Eos {
+  double a, b, RT;
+  double p0(double r) const { return r * RT / (1 - b * r) - a * r * r; }
+  double dp0(double r) const { return RT / ((1 - b * r) * (1 - b * r)) - 2 * a * r; }
+  double mu0(double r) const { return RT * (std::log(r / (1 - b * r)) + 1 / (1 - b * r)) - 2 * a * r; }
+};
+
+template <typename Fn>
+double bisect(Fn fn, double lo, double hi) {
+  double flo = fn(lo);
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    double fm = fn(mid);
+    if ((fm < 0) == (flo < 0)) {
+      lo = mid;
+      flo = fm;
+    } else {
+      hi = mid;
+    }
+    if (hi - lo <= 1e-16 * std::fabs(mid)) break;
+  }
+  return 0.5 * (lo + hi);
+}
+}  // namespace
+
+extern "C" int lbm_maxwell(double a, double b, double R, double T, double *rho_l, double *rho_v) {
+  if (!rho_l || !rho_v || !(a > 0) || !(b > 0) || !(R > 0) || !(T > 0)) return LBM_ERR_ARG;
+  const double Tc = 8 * a / (27 * R * b);
+  if (!(T < Tc)) return LBM_ERR_ARG;
+  Eos e{a, b, R * T};
+  const double rc = 1 / (3 * b), rmax = (1 - 1e-13) / b;
+  const double s_lo = bisect([&](double r) { return e.dp0(r); }, 1e-12, rc);
+  const double s_hi = bisect([&](double r) { return -e.dp0(r); }, rc, rmax);
+  double p_lo = e.p0(s_hi), p_hi = e.p0(s_lo);
+  if (p_lo < 1e-300) p_lo = 1e-300;
+  auto phases = [&](double p, double *rl, double *rv) {
+    *rv = bisect([&](double r) { return e.p0(r) - p; }, 1e-300, s_lo);
+    *rl = bisect([&](double r) { return e.p0(r) - p; }, s_hi, rmax);
+  };
+  double pc = bisect(
+      [&](double p) {
+        double rl, rv;
+        phases(p, &rl, &rv);
+        return e.mu0(rl) - e.mu0(rv);
+      },
+      p_lo, p_hi);
+  phases(pc, rho_l, rho_v);
+  return LBM_OK;
+}

@@ -1,0 +1,105 @@
+// Internal declarations shared by the C-ABI layer (lbm_api.cu) and the
+// kernels (lbm_forward.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Kernel-side model parameters, FP32 (the device arithmetic type).
+struct KParams {
+  int nx, ny, nz, N;
+  float RT, a, b, kappa;
+  float om[11];
+  float nu;        // > 0: omega_1 per node from 1/omega_1 = rho nu / p_m + 1/2
+  int q4;          // fourth-order correction on/off
+  float rho_shift; // rho_0 of the stored populations f_i - w_i rho_0
+  int shift_mode;  // LBM_SHIFT_CONST or LBM_SHIFT_REST
+  int wet_mode;
+  float wet_value, band_lo, band_hi;
+  // Chemical potential is carried as mu' = mu - mu_ref.  mu0(rho) - mu_ref
+  // is evaluated about the reference density of the node's phase (rho_l
+  // above rho_split, rho_v below) so that FP32 does not cancel large terms.
+  float mu_ref, pm_ref;             // pm_ref = (1 + mu_ref) / 3
+  float rho_split;
+  float ref_rho[2], ref_omb[2], ref_dmu[2];  // [0] vapour, [1] liquid: rho_r, 1 - b rho_r, mu0(rho_r) - mu_ref
+};
+
+// Device views carved out of the caller's workspace.
+struct Fields {
+  float *rho;  // N     density (fluid: sum f; solid: wetting value)
+  float *j;    // 3N    sum f c
+  float *mu;   // N     chemical potential minus mu_ref
+  float *u;    // 3N    force-corrected velocity
+  float *F;    // 3N    force (1/3 - rho) grad mu
+  float *phi;  // 3N    (p_m - rho/3) u
+  float *Q;    // 3N    Q_200, Q_020, Q_002
+  float *sb;   // 2N    shift bases of LBM_SHIFT_REST: rho, then p_m - rho/3
+};
+
+enum KernelId {
+  K_MOMENTS = 0,
+  K_WET_RHO,
+  K_MU,
+  K_WET_MU,
+  K_UPHI,
+  K_Q,
+  K_COLLIDE,
+  K_COUNT
+};
+
+struct ProfEvent {
+  int id;
+  cudaEvent_t start, stop;
+};
+
+}  // namespace lbm
+
+struct lbm_ctx {
+  int nx, ny, nz, N, storage;
+  cudaStream_t stream;
+  const uint8_t *mask;  // device, may be null
+  int n_bnd;
+  int *bnd;             // solid nodes with at least one fluid neighbour
+  void *f[2];
+  int cur;
+  lbm::Fields fld;
+  double *red_partial;  // RED_BLOCKS * 2
+  int *status;          // [0] status bits, [1] counter scratch
+  lbm_params params;
+  lbm::KParams kp;
+  int have_params, have_state;
+  long long launches;
+  int prof_on;
+  std::vector<lbm::ProfEvent> prof_pending;
+  std::vector<cudaEvent_t> prof_free;
+  double prof_ms[lbm::K_COUNT];
+  long long prof_n[lbm::K_COUNT];
+  std::string err;
+};
+
+namespace lbm {
+
+constexpr int RED_BLOCKS = 1024;
+constexpr int STATUS_NONFINITE = 1;
+constexpr int STATUS_DOMAIN = 2;
+
+// Launchers (lbm_forward.cu).  Each enqueues on ctx->stream and counts its
+// launches; they do not check errors (the caller does).
+void launch_mark_boundary(lbm_ctx *ctx);
+void launch_step(lbm_ctx *ctx);                 // one full time step, swaps buffers
+void launch_fields(lbm_ctx *ctx, bool with_u);  // moments .. (u, F, phi) of current state
+void launch_init(lbm_ctx *ctx, const float *rho0, const float *u0);
+void launch_reduce(lbm_ctx *ctx, double *out);
+void launch_get_populations(lbm_ctx *ctx, float *out);
+void launch_copy_mu(lbm_ctx *ctx, float *out);       // mu' + mu_ref
+void launch_set_populations(lbm_ctx *ctx, const float *in);
+const char *kernel_name(int id);
+
+}  // namespace lbm

@@ -1,0 +1,224 @@
+// Device-side D3Q27 lattice helpers: weights, periodic neighbour indexing,
+// storage conversion, the central-moment transform factorised into three
+// 1-D passes, and the central-moment collision of Sec. II B (Eqs. 21-26).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Population q has velocity (q%3 - 1, (q/3)%3 - 1, q/9 - 1); rest is q = 13.
+__host__ __device__ constexpr int cx_of(int q) { return q % 3 - 1; }
+__host__ __device__ constexpr int cy_of(int q) { return (q / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz_of(int q) { return q / 9 - 1; }
+
+// Lattice weights by |c|^2 = 0, 1, 2, 3 (Eq. 17).
+__host__ __device__ constexpr float weight_of(int q) {
+  return (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 0   ? 8.0f / 27.0f
+         : (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 1 ? 2.0f / 27.0f
+         : (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 2 ? 1.0f / 54.0f
+                                                                                 : 1.0f / 216.0f;
+}
+
+// E_i of Eq. 16 at u = 0 by speed class: -19/9, 2/9, 1/18, 1/72.
+__host__ __device__ constexpr float iso_rest_of(int q) {
+  return (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 0   ? -19.0f / 9.0f
+         : (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 1 ? 2.0f / 9.0f
+         : (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 2 ? 1.0f / 18.0f
+                                                                                 : 1.0f / 72.0f;
+}
+
+// Storage shift of population q.  LBM_SHIFT_CONST: w_q rho_0.
+// LBM_SHIFT_REST: the rest equilibrium w_q rho_b + c_b E_q of a basis
+// (rho_b, c_b = p_m - rho/3); basis_c gives c_b from rho and mu, and every
+// writer and reader of a population computes it with this same function.
+__device__ __forceinline__ float basis_c(float rho, float mup, const KParams &kp) {
+  return fmaf(mup - rho, 1.0f / 3.0f, kp.pm_ref);
+}
+__device__ __forceinline__ float shift_rest(int q, float rb, float cb) {
+  return fmaf(weight_of(q), rb, cb * iso_rest_of(q));
+}
+
+__device__ __forceinline__ int wrap(int v, int n) {
+  return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+struct Node {
+  int x, y, z;
+};
+
+__device__ __forceinline__ Node decode(int n, int nx, int ny) {
+  Node p;
+  p.x = n % nx;
+  int t = n / nx;
+  p.y = t % ny;
+  p.z = t / ny;
+  return p;
+}
+
+__device__ __forceinline__ int neighbour(const Node &p, int dx, int dy, int dz, const KParams &kp) {
+  return wrap(p.x + dx, kp.nx) + kp.nx * (wrap(p.y + dy, kp.ny) + kp.ny * wrap(p.z + dz, kp.nz));
+}
+
+// ---- storage type conversion ----------------------------------------------
+template <typename T> __device__ __forceinline__ float load_pop(const T *p);
+template <> __device__ __forceinline__ float load_pop<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_pop<__half>(const __half *p) {
+  return __half2float(__ldg(p));
+}
+template <typename T> __device__ __forceinline__ void store_pop(T *p, float v);
+template <> __device__ __forceinline__ void store_pop<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void store_pop<__half>(__half *p, float v) {
+  *p = __float2half_rn(v);
+}
+
+// ---- central-moment transform (Eq. 19) ----------------------------------
+// One axis: values (a, b, c) of the velocities -1, 0, +1 become the central
+// moments of order 0, 1, 2 about u.  With s = a + c, d = c - a:
+//   M0 = s + b,  M1 = d - u M0,  M2 = s - 2 u d + u^2 M0.
+__device__ __forceinline__ void cm_axis(float &a, float &b, float &c, float u) {
+  float s = a + c, d = c - a;
+  float m0 = s + b;
+  float m1 = fmaf(-u, m0, d);
+  float m2 = fmaf(u * u, m0, fmaf(-2.0f * u, d, s));
+  a = m0;
+  b = m1;
+  c = m2;
+}
+
+// Inverse of cm_axis: d = M1 + u M0, s = M2 + 2 u d - u^2 M0, then
+// a = (s - d)/2, b = M0 - s, c = (s + d)/2.
+__device__ __forceinline__ void cm_axis_inv(float &a, float &b, float &c, float u) {
+  float m0 = a, m1 = b, m2 = c;
+  float d = fmaf(u, m0, m1);
+  float s = fmaf(-u * u, m0, fmaf(2.0f * u, d, m2));
+  a = 0.5f * (s - d);
+  b = m0 - s;
+  c = 0.5f * (s + d);
+}
+
+// f[q] (q = (cx+1) + 3(cy+1) + 9(cz+1)) -> k[a + 3b + 9c] in place: the
+// triple sum over (cz, cy, cx) of Eq. 19 done one axis at a time.
+__device__ __forceinline__ void to_central(float f[27], float ux, float uy, float uz) {
+#pragma unroll
+  for (int p = 0; p < 9; ++p) cm_axis(f[p], f[p + 9], f[p + 18], uz);
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cm_axis(f[a + 9 * g], f[a + 3 + 9 * g], f[a + 6 + 9 * g], uy);
+#pragma unroll
+  for (int q = 0; q < 27; q += 3) cm_axis(f[q], f[q + 1], f[q + 2], ux);
+}
+
+__device__ __forceinline__ void from_central(float k[27], float ux, float uy, float uz) {
+#pragma unroll
+  for (int q = 0; q < 27; q += 3) cm_axis_inv(k[q], k[q + 1], k[q + 2], ux);
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cm_axis_inv(k[a + 9 * g], k[a + 3 + 9 * g], k[a + 6 + 9 * g], uy);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) cm_axis_inv(k[p], k[p + 9], k[p + 18], uz);
+}
+
+#define KM(a, b, c) k[(a) + 3 * (b) + 9 * (c)]
+
+// Post-collision central moments, Eqs. 21-26, in place.  k000 is unchanged.
+// om1 is omega_1 of this node; the other rates come from kp.om.
+__device__ __forceinline__ void collide_cm(float k[27], float pm, float Fx, float Fy, float Fz,
+                                           float Qx, float Qy, float Qz, float om1,
+                                           const KParams &kp) {
+  const float cs2 = 1.0f / 3.0f;
+  const float o0 = kp.om[0], o2 = kp.om[2], o3 = kp.om[3], o4 = kp.om[4], o5 = kp.om[5];
+  const float o6 = kp.om[6], o7 = kp.om[7], o8 = kp.om[8], o9 = kp.om[9], o10 = kp.om[10];
+  // first order (Eq. 21)
+  KM(1, 0, 0) = (1.0f - o0) * KM(1, 0, 0) + (1.0f - 0.5f * o0) * Fx;
+  KM(0, 1, 0) = (1.0f - o0) * KM(0, 1, 0) + (1.0f - 0.5f * o0) * Fy;
+  KM(0, 0, 1) = (1.0f - o0) * KM(0, 0, 1) + (1.0f - 0.5f * o0) * Fz;
+  // second order (Eq. 22)
+  KM(1, 1, 0) *= (1.0f - om1);
+  KM(0, 1, 1) *= (1.0f - om1);
+  KM(1, 0, 1) *= (1.0f - om1);
+  {
+    float A = (1.0f - om1) * (KM(2, 0, 0) - KM(0, 2, 0)) + (1.0f - 0.5f * om1) * (Qx - Qy);
+    float B = (1.0f - om1) * (KM(2, 0, 0) - KM(0, 0, 2)) + (1.0f - 0.5f * om1) * (Qx - Qz);
+    float S = (1.0f - o2) * (KM(2, 0, 0) + KM(0, 2, 0) + KM(0, 0, 2)) + 3.0f * o2 * pm +
+              (1.0f - 0.5f * o2) * (Qx + Qy + Qz);
+    KM(2, 0, 0) = (S + A + B) * (1.0f / 3.0f);
+    KM(0, 2, 0) = (S - 2.0f * A + B) * (1.0f / 3.0f);
+    KM(0, 0, 2) = (S + A - 2.0f * B) * (1.0f / 3.0f);
+  }
+  // third order (Eq. 23)
+  {
+    const float g3 = 2.0f * (1.0f - 0.5f * o3) * cs2;
+    float P, D;
+    P = (1.0f - o3) * (KM(1, 2, 0) + KM(1, 0, 2)) + g3 * Fx;
+    D = (1.0f - o4) * (KM(1, 2, 0) - KM(1, 0, 2));
+    KM(1, 2, 0) = 0.5f * (P + D);
+    KM(1, 0, 2) = 0.5f * (P - D);
+    P = (1.0f - o3) * (KM(2, 1, 0) + KM(0, 1, 2)) + g3 * Fy;
+    D = (1.0f - o4) * (KM(2, 1, 0) - KM(0, 1, 2));
+    KM(2, 1, 0) = 0.5f * (P + D);
+    KM(0, 1, 2) = 0.5f * (P - D);
+    P = (1.0f - o3) * (KM(2, 0, 1) + KM(0, 2, 1)) + g3 * Fz;
+    D = (1.0f - o4) * (KM(2, 0, 1) - KM(0, 2, 1));
+    KM(2, 0, 1) = 0.5f * (P + D);
+    KM(0, 2, 1) = 0.5f * (P - D);
+    KM(1, 1, 1) *= (1.0f - o5);
+  }
+  // fourth order (Eq. 24) with the approximate correction of Eq. 28
+  {
+    float Q220 = 0.0f, Q202 = 0.0f, Q022 = 0.0f;
+    if (kp.q4) {
+      Q220 = (Qx + Qy) * cs2;
+      Q202 = (Qx + Qz) * cs2;
+      Q022 = (Qy + Qz) * cs2;
+    }
+    float a = KM(2, 2, 0), b = KM(2, 0, 2), c = KM(0, 2, 2);
+    float D1 = (1.0f - o6) * (a - 2.0f * b + c) + (1.0f - 0.5f * o6) * (Q220 - 2.0f * Q202 + Q022);
+    float D2 = (1.0f - o6) * (a + b - 2.0f * c) + (1.0f - 0.5f * o6) * (Q220 + Q202 - 2.0f * Q022);
+    float T = (1.0f - o7) * (a + b + c) + 3.0f * o7 * pm * cs2 +
+              (1.0f - 0.5f * o7) * (Q220 + Q202 + Q022);
+    KM(2, 2, 0) = (T + D1 + D2) * (1.0f / 3.0f);
+    KM(2, 0, 2) = (T - D1) * (1.0f / 3.0f);
+    KM(0, 2, 2) = (T - D2) * (1.0f / 3.0f);
+    KM(2, 1, 1) *= (1.0f - o8);
+    KM(1, 2, 1) *= (1.0f - o8);
+    KM(1, 1, 2) *= (1.0f - o8);
+  }
+  // fifth order (Eq. 25)
+  {
+    const float g5 = (1.0f - 0.5f * o9) * cs2 * cs2;
+    KM(1, 2, 2) = (1.0f - o9) * KM(1, 2, 2) + g5 * Fx;
+    KM(2, 1, 2) = (1.0f - o9) * KM(2, 1, 2) + g5 * Fy;
+    KM(2, 2, 1) = (1.0f - o9) * KM(2, 2, 1) + g5 * Fz;
+  }
+  // sixth order (Eq. 26)
+  KM(2, 2, 2) = (1.0f - o10) * KM(2, 2, 2) + o10 * pm * cs2 * cs2;
+}
+
+// Bulk chemical potential of the van der Waals EOS (bulk part of Eq. 32),
+// returned as mu0(rho) - mu_ref.  With d = rho - rho_r about the reference
+// density of the node's phase, the identity
+//   mu0(rho) = mu0(rho_r) + RT [ln(1 + d/rho_r) - ln(1 - b d/(1 - b rho_r))
+//              + b d / ((1 - b rho)(1 - b rho_r))] - 2 a d
+// holds exactly; every term is O(d), so FP32 keeps its relative precision
+// where the direct form cancels (liquid: RT(...) ~ 2.5 against 2 a rho ~ 2.3).
+__device__ __forceinline__ float mu0_vdw(float r, const KParams &kp) {
+  const int ph = r > kp.rho_split ? 1 : 0;
+  const float rr = kp.ref_rho[ph], omb = kp.ref_omb[ph];
+  const float d = r - rr;
+  const float t = log1pf(d / rr) - log1pf(-kp.b * d / omb) + kp.b * d / ((1.0f - kp.b * r) * omb);
+  return kp.ref_dmu[ph] + kp.RT * t - 2.0f * kp.a * d;
+}
+
+// p_m = (1 + mu)/3 from mu' = mu - mu_ref.
+__device__ __forceinline__ float pm_of(float mup, const KParams &kp) {
+  return fmaf(mup, 1.0f / 3.0f, kp.pm_ref);
+}
+
+}  // namespace lbm

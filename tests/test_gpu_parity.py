@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle,
+element by element, on the same seeded FP32-representable inputs.
+
+Tolerances.  The device computes in FP32 (unit roundoff 6e-8).  One step of
+the model is a few hundred dependent operations per node whose inputs carry
+magnitudes up to ~7 (liquid density), so a single step is expected within a
+few 1e-7 relative; the bounds below are the targets of the method's precision
+contract (max relative rho error 1e-5 and |du| <= 1e-6 lattice units for FP32
+storage; 1e-3 relative rho for FP16 storage) unless a tighter per-step bound
+is stated.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import step as S
+from paper_2504_03819_gb300 import Domain
+from paper_2504_03819_gb300 import inputs as I
+
+from _cases import CASES, build, oracle_init, oracle_params, perturbed
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu(case, storage="f32"):
+    nx, ny, nz = case["n"]
+    d = Domain(nx, ny, nz, storage, solid_mask=case["mask"] if case["mask"].any() else None)
+    d.set_params(case["p"])
+    return d
+
+
+def rel(a, b, floor=1e-3):
+    a, b = a.double().cpu(), b.double().cpu()
+    return float(((a - b).abs() / b.abs().clamp_min(floor)).max())
+
+
+def absd(a, b):
+    return float((a.double().cpu() - b.double().cpu()).abs().max())
+
+
+def fluid(case):
+    return torch.from_numpy(~case["mask"].astype(bool))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_initial_populations(name):
+    case = build(name)
+    d = gpu(case)
+    d.set_state(torch.from_numpy(case["rho0"]).float(), torch.from_numpy(case["u0"]).float())
+    got = d.get_populations()
+    ref = oracle_init(case)
+    scale = float(ref.abs().max())
+    assert absd(got, ref) / scale < 1e-6
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fields_of_a_state(name):
+    """lbm_moments on an arbitrary (non-equilibrium) state: rho, u, mu and the
+    FP64 mass / energy against oracle.macroscopic of the same populations."""
+    case = build(name)
+    fr = perturbed(case, oracle_init(case), seed=11)
+    d = gpu(case)
+    d.set_populations(fr.float())
+    m = d.moments()
+    solid = torch.from_numpy(case["mask"].astype(bool))
+    ref = S.macroscopic(fr, solid, oracle_params(case["p"]))
+    assert rel(m["rho"], ref["rho"]) < 1e-6
+    assert absd(m["u"], ref["u"]) < 1e-7
+    assert absd(m["mu"], ref["mu"]) < 1e-6
+    assert m["mass"] == pytest.approx(float(ref["mass"]), rel=1e-6)
+    assert m["energy"] == pytest.approx(float(ref["energy"]), rel=1e-4, abs=1e-9)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_from_nonequilibrium_state(name):
+    """Every population after one step from the same perturbed state."""
+    case = build(name)
+    fr = perturbed(case, oracle_init(case), seed=21)
+    d = gpu(case)
+    d.set_populations(fr.float())
+    d.step(1)
+    assert d.sync_status() == 0
+    got = d.get_populations()
+    solid = torch.from_numpy(case["mask"].astype(bool))
+    ref = S.step(fr, solid, oracle_params(case["p"]))
+    scale = float(ref.abs().max())
+    assert absd(got, ref) / scale < 2e-6
+
+
+# Conditioning: FP32-sized noise (6e-8 relative) in the initial state grows
+# in the FP64 oracle itself, after 50 steps, to ~2e-6 relative density for
+# wall_neutral_rates_noq4 (no fourth-order correction, curved interface: the
+# setting Sec. III B reports as unstable) and to <= 8e-7 for the other cases.
+# The bound for that case is scaled by the same factor.
+RHO_TOL_50 = {"wall_neutral_rates_noq4": 5e-5}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fifty_steps_from_init(name):
+    case = build(name)
+    d = gpu(case)
+    d.set_state(torch.from_numpy(case["rho0"]).float(), torch.from_numpy(case["u0"]).float())
+    d.step(50)
+    assert d.sync_status() == 0
+    m = d.moments()
+    solid = torch.from_numpy(case["mask"].astype(bool))
+    op = oracle_params(case["p"])
+    f = S.run(oracle_init(case), solid, op, 50)
+    ref = S.macroscopic(f, solid, op)
+    fl = fluid(case)
+    assert rel(m["rho"][fl], ref["rho"][fl]) < RHO_TOL_50.get(name, 1e-5)
+    assert absd(m["u"], ref["u"]) < 1e-6
+    assert m["mass"] == pytest.approx(float(ref["mass"]), rel=1e-6)
+
+
+def test_flat_interface_thousand_steps():
+    """Flat-interface workload (8 x 8 x 128, a = 9/49, kappa = 0.01, 0.85 T_c,
+    slab of width 64) for 1000 steps: the density profile is uniform in x, y,
+    so the oracle runs the same problem exactly on 1 x 1 x 128."""
+    from _cases import vdw
+    p = vdw()
+    nz = 128
+    rho1d = I.slab(1, 1, nz, 64, p.rho_l, p.rho_v).astype(np.float32)
+    d = Domain(8, 8, nz, "f32")
+    d.set_params(p)
+    d.set_state(torch.from_numpy(np.repeat(np.repeat(rho1d, 8, axis=1), 8, axis=2)))
+    d.step(1000)
+    assert d.sync_status() == 0
+    m = d.moments()
+    op = oracle_params(p)
+    solid = torch.zeros(nz, 1, 1, dtype=torch.bool)
+    f = S.run(S.initial_populations(torch.from_numpy(rho1d.astype(np.float64)), None, solid, op), solid, op, 1000)
+    ref = S.macroscopic(f, solid, op)
+    r_ref = ref["rho"].expand(nz, 8, 8)
+    assert rel(m["rho"], r_ref) < 1e-5
+    assert absd(m["u"], ref["u"].expand(3, nz, 8, 8)) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["droplet_periodic", "wall_phi"])
+def test_constant_shift_mode_fifty_steps(name):
+    """Populations stored as f_i - w_i rho_0 (rho_0 = harmonic mean of the
+    coexistence densities) give the same trajectory within FP32 bounds."""
+    case = build(name)
+    p = case["p"]
+    p.shift_mode = 0
+    p.rho_shift = 2 * p.rho_l * p.rho_v / (p.rho_l + p.rho_v)
+    d = gpu(case)
+    d.set_state(torch.from_numpy(case["rho0"]).float(), torch.from_numpy(case["u0"]).float())
+    d.step(50)
+    assert d.sync_status() == 0
+    m = d.moments()
+    solid = torch.from_numpy(case["mask"].astype(bool))
+    op = oracle_params(p)
+    ref = S.macroscopic(S.run(oracle_init(case), solid, op, 50), solid, op)
+    fl = fluid(case)
+    assert rel(m["rho"][fl], ref["rho"][fl]) < 1e-5
+    assert absd(m["u"], ref["u"]) < 1e-6
+
+
+def test_fp16_storage_fifty_steps():
+    case = build("droplet_periodic")
+    p = case["p"]
+    d = gpu(case, "f16")
+    d.set_state(torch.from_numpy(case["rho0"]).float(), torch.from_numpy(case["u0"]).float())
+    d.step(50)
+    assert d.sync_status() == 0
+    m = d.moments()
+    solid = torch.from_numpy(case["mask"].astype(bool))
+    op = oracle_params(p)
+    ref = S.macroscopic(S.run(oracle_init(case), solid, op, 50), solid, op)
+    assert rel(m["rho"], ref["rho"]) < 1e-3
+
+
+def test_status_flags():
+    case = build("droplet_periodic")
+    d = gpu(case)
+    f = oracle_init(case).float()
+    d.set_populations(f)
+    d.step(2)
+    assert d.sync_status() == 0
+    bad = f.clone()
+    bad[:, 3, 4, 5] = float("nan")
+    d.set_populations(bad)
+    d.step(1)
+    assert d.sync_status() == -4  # LBM_ERR_NONFINITE
+    big = f.clone()
+    big[13, 2, 2, 2] = 20.0  # rho > 1/b = 10.5
+    d.set_populations(big)
+    d.step(1)
+    assert d.sync_status() == -5  # LBM_ERR_DOMAIN
+
+
+def test_raw_state_roundtrip_and_determinism():
+    case = build("wall_phi")
+    d = gpu(case)
+    d.set_state(torch.from_numpy(case["rho0"]).float())
+    d.step(5)
+    s0 = d.get_state().clone()
+    d.step(7)
+    a = d.get_state().clone()
+    d.set_raw_state(s0)
+    d.step(7)
+    b = d.get_state()
+    assert torch.equal(a, b)
+
+
+def test_zero_steps_is_noop():
+    case = build("wall_phi")
+    d = gpu(case)
+    d.set_state(torch.from_numpy(case["rho0"]).float())
+    s0 = d.get_state().clone()
+    n0 = d.launch_count()
+    d.step(0)
+    assert d.launch_count() == n0
+    assert torch.equal(d.get_state(), s0)
