@@ -209,6 +209,46 @@ int lbm_profile_read(lbm_ctx *ctx, int id, double *total_ms, long long *launches
 /* Name of kernel `id` of the step, or NULL past the last one. */
 const char *lbm_kernel_name(int id);
 
+/* ---- a step without device allocation ----------------------------------- */
+
+/* Largest domain (nx*ny*nz) lbm_step_noalloc accepts. */
+#define LBM_NOALLOC_MAX_NODES 32768
+
+/*
+ * One time step for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a packaging of lbm_step for code that is not
+ * allowed to call cudaMalloc or a caching allocator (for example a plugin or
+ * solver kernel embedded in a host application that owns every device
+ * allocation, or code running under a fixed memory budget), so it cannot
+ * provide the workspace of lbm_init_domain.
+ *
+ * Runs the same kernels as lbm_step with LBM_F32 storage on unshifted
+ * populations (params->shift_mode and rho_shift are ignored).  The step's
+ * scratch (the macroscopic fields and the boundary list, about 2.6 MB) lives
+ * in one static device array of the library, sized for
+ * LBM_NOALLOC_MAX_NODES nodes; every GPU that loads the library holds it
+ * until the process exits.
+ *  f_in        device, 27*N floats: populations f_i at time t (layout as in
+ *              the conventions above); read only.
+ *  f_out       device, 27*N floats, must not alias f_in: populations at
+ *              t + 1; solid-node slots are set to 0.
+ *  solid_mask  device, N bytes, or NULL for an all-fluid domain.
+ *  params      host; validated as by lbm_set_params.
+ *  cuda_stream stream to enqueue on (NULL = default stream).
+ * Returns LBM_ERR_SIZE if nx*ny*nz > LBM_NOALLOC_MAX_NODES, LBM_ERR_ARG for
+ * invalid arguments (no message: there is no context), LBM_ERR_CUDA if a
+ * CUDA call fails.  With a solid mask it synchronises the stream once (to
+ * count boundary nodes).  Calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ * The first call on each device looks up the device address of the static
+ * array (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call shares the one array, so calls
+ * whose work overlaps on the GPU (different streams, threads or processes
+ * sharing a context) race and give wrong results: serialise them.
+ */
+int lbm_step_noalloc(const float *f_in, float *f_out, const uint8_t *solid_mask, int nx, int ny, int nz,
+                     const lbm_params *params, void *cuda_stream);
+
 /* ---- host helpers ------------------------------------------------------- */
 
 /*

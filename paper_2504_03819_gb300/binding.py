@@ -43,6 +43,8 @@ SIGNATURES = {
     "lbm_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_kernel_name": (C.c_char_p, [C.c_int]),
+    "lbm_step_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                   C.c_void_p]),
     "lbm_maxwell": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
                               C.POINTER(C.c_double)]),
 }
@@ -133,6 +135,27 @@ class Params:
 
 def _ptr(t) -> C.c_void_p:
     return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+NOALLOC_MAX_NODES = 32768
+
+
+def step_noalloc(f_in, f_out, solid_mask, params: Params, stream=None) -> int:
+    """One step through lbm_step_noalloc, for callers that cannot allocate
+    device memory (the library keeps the scratch in a static device array).
+    f_in, f_out: CUDA float32 tensors (27, nz, ny, nx); solid_mask: CUDA uint8
+    (nz, ny, nx) or None.  Returns the LBM_* status code."""
+    import torch
+    for name, t in (("f_in", f_in), ("f_out", f_out), ("solid_mask", solid_mask)):
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor (no copy is made)")
+    if f_in.dtype != torch.float32 or f_out.dtype != torch.float32 or f_in.shape != f_out.shape:
+        raise ValueError("f_in and f_out must be float32 tensors of the same shape (27, nz, ny, nx)")
+    _, nz, ny, nx = f_in.shape
+    pc = params.to_c()
+    s = stream if stream is not None else torch.cuda.current_stream(f_in.device)
+    return load().lbm_step_noalloc(_ptr(f_in), _ptr(f_out), _ptr(solid_mask), nx, ny, nz, C.byref(pc),
+                                   C.c_void_p(s.cuda_stream))
 
 
 class Domain:
