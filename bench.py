@@ -30,10 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D3Q27 FE-LBM MLUPS & % of HBM peak (FP32/FP16-store); adjoint/forward time"
 ALG_BYTES = {"f32": 216, "f16": 108}   # read + write of 27 populations per lattice update
-WORKLOAD = dict(n=(256, 256, 256), radius=32.0, u=(0.05, 0.02, 0.0), t_over_tc=0.85, a=9.0 / 49.0,
+WORKLOAD = dict(n=(256, 256, 256), radius=32.0, width=2.0, u=(0.05, 0.02, 0.0), t_over_tc=0.85, a=9.0 / 49.0,
                 b=2.0 / 21.0, R=1.0, kappa=0.01, omega1=1.6)
-WORKLOAD_NAME = ("moving droplet 256^3 periodic, R=32, U=(0.05,0.02,0), vdW a=9/49 b=2/21 T=0.85Tc, "
-                 "kappa=0.01, omega1=1.6, other rates 1")
+WORKLOAD_NAME = ("moving droplet 256^3 periodic, R=32 (tanh width 2), U=(0.05,0.02,0), vdW a=9/49 b=2/21 "
+                 "T=0.85Tc, kappa=0.01, omega1=1.6, other rates 1")
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
 # storage, valid only while the kernel sources hash to `src`.
@@ -69,7 +69,7 @@ def workload_params(storage: str):
     p = Params.vdw(w["a"], w["b"], w["R"], w["t_over_tc"], w["kappa"], omega=om)
     p.rho_shift = 2.0 * p.rho_l * p.rho_v / (p.rho_l + p.rho_v)
     nx, ny, nz = w["n"]
-    rho0 = I.droplet(nx, ny, nz, w["radius"], p.rho_l, p.rho_v).astype(np.float32)
+    rho0 = I.droplet(nx, ny, nz, w["radius"], p.rho_l, p.rho_v, width=w["width"]).astype(np.float32)
     u0 = I.uniform_velocity(nx, ny, nz, w["u"]).astype(np.float32)
     return p, rho0, u0
 
@@ -250,7 +250,7 @@ def cpu_sample(nx: int, ny: int, nz: int, nsteps: int):
     full = w["n"]
     # the slab through the droplet centre of the full workload, same node values
     z0 = full[2] // 2 - nz // 2
-    rho = I.droplet(full[0], full[1], full[2], w["radius"], rl, rv)[z0:z0 + nz, :ny, :nx]
+    rho = I.droplet(full[0], full[1], full[2], w["radius"], rl, rv, width=w["width"])[z0:z0 + nz, :ny, :nx]
     u0 = I.uniform_velocity(nx, ny, nz, w["u"])
     solid = torch.zeros(nz, ny, nx, dtype=torch.bool)
     f = S.initial_populations(torch.from_numpy(np.ascontiguousarray(rho)), torch.from_numpy(u0), solid, p)

@@ -406,37 +406,6 @@ __global__ void __launch_bounds__(RED_BLOCKS) k_reduce_final(const double *__res
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-cudaEvent_t take_event(lbm_ctx *ctx) {
-  if (ctx->prof_free.empty()) {
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-  }
-  cudaEvent_t e = ctx->prof_free.back();
-  ctx->prof_free.pop_back();
-  return e;
-}
-
-struct Timed {
-  lbm_ctx *ctx;
-  ProfEvent ev;
-  Timed(lbm_ctx *c, int id) : ctx(c) {
-    ev.id = id;
-    if (ctx->prof_on) {
-      ev.start = take_event(ctx);
-      ev.stop = take_event(ctx);
-      cudaEventRecord(ev.start, ctx->stream);
-    }
-    ctx->launches++;
-  }
-  ~Timed() {
-    if (ctx->prof_on) {
-      cudaEventRecord(ev.stop, ctx->stream);
-      ctx->prof_pending.push_back(ev);
-    }
-  }
-};
-
 template <typename T>
 void step_impl(lbm_ctx *ctx) {
   const KParams &kp = ctx->kp;
@@ -445,13 +414,13 @@ void step_impl(lbm_ctx *ctx) {
   T *fout = (T *)ctx->f[1 - ctx->cur];
   const int g = blocks_for(kp.N);
   cudaStream_t s = ctx->stream;
-  { Timed t(ctx, K_MOMENTS); k_moments<T><<<g, BLOCK, 0, s>>>(fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp); }
-  if (ctx->n_bnd) { Timed t(ctx, K_WET_RHO); k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.rho, kp); }
-  { Timed t(ctx, K_MU); k_mu<<<g, BLOCK, 0, s>>>(d.rho, ctx->mask, d.mu, kp); }
-  if (ctx->n_bnd) { Timed t(ctx, K_WET_MU); k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.mu, kp); }
-  { Timed t(ctx, K_UPHI); k_uphi<<<g, BLOCK, 0, s>>>(d.rho, d.j, d.mu, ctx->mask, d.u, d.F, d.phi, kp); }
-  { Timed t(ctx, K_Q); k_q<<<g, BLOCK, 0, s>>>(d.phi, ctx->mask, d.Q, kp); }
-  { Timed t(ctx, K_COLLIDE); k_collide<T><<<g, BLOCK, 0, s>>>(fin, fout, ctx->mask, d.rho, d.u, d.F, d.mu, d.Q, d.sb, kp); }
+  { TimedLaunch t(ctx, K_MOMENTS); k_moments<T><<<g, BLOCK, 0, s>>>(fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp); }
+  if (ctx->n_bnd) { TimedLaunch t(ctx, K_WET_RHO); k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.rho, kp); }
+  { TimedLaunch t(ctx, K_MU); k_mu<<<g, BLOCK, 0, s>>>(d.rho, ctx->mask, d.mu, kp); }
+  if (ctx->n_bnd) { TimedLaunch t(ctx, K_WET_MU); k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.mu, kp); }
+  { TimedLaunch t(ctx, K_UPHI); k_uphi<<<g, BLOCK, 0, s>>>(d.rho, d.j, d.mu, ctx->mask, d.u, d.F, d.phi, kp); }
+  { TimedLaunch t(ctx, K_Q); k_q<<<g, BLOCK, 0, s>>>(d.phi, ctx->mask, d.Q, kp); }
+  { TimedLaunch t(ctx, K_COLLIDE); k_collide<T><<<g, BLOCK, 0, s>>>(fin, fout, ctx->mask, d.rho, d.u, d.F, d.mu, d.Q, d.sb, kp); }
   ctx->cur = 1 - ctx->cur;
 }
 
@@ -481,11 +450,25 @@ void launch_mark_boundary(lbm_ctx *ctx) {
   ctx->launches++;
 }
 
-void launch_step(lbm_ctx *ctx) {
+void launch_step(lbm_ctx *ctx) { launch_step_fused(ctx); }
+
+// The seven-kernel form of the step (one kernel per stage, fields through
+// global memory).  Not on the lbm_step path; kept for stage-by-stage checks.
+void launch_step_staged(lbm_ctx *ctx) {
   if (ctx->storage == LBM_F16)
     step_impl<__half>(ctx);
   else
     step_impl<float>(ctx);
+}
+
+void launch_wet_rho(lbm_ctx *ctx) {
+  TimedLaunch t(ctx, K_WET_RHO);
+  k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld.rho, ctx->kp);
+}
+
+void launch_wet_mu(lbm_ctx *ctx) {
+  TimedLaunch t(ctx, K_WET_MU);
+  k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld.mu, ctx->kp);
 }
 
 void launch_fields(lbm_ctx *ctx, bool with_u) {

@@ -94,6 +94,11 @@ constexpr int STATUS_DOMAIN = 2;
 // launches; they do not check errors (the caller does).
 void launch_mark_boundary(lbm_ctx *ctx);
 void launch_step(lbm_ctx *ctx);                 // one full time step, swaps buffers
+void launch_step_fused(lbm_ctx *ctx);           // the three-kernel step (lbm_step_fused.cu)
+void launch_step_staged(lbm_ctx *ctx);          // the seven-kernel step (lbm_forward.cu)
+void launch_wet_rho(lbm_ctx *ctx);
+void launch_wet_mu(lbm_ctx *ctx);
+size_t fused_smem_bytes();
 void launch_fields(lbm_ctx *ctx, bool with_u);  // moments .. (u, F, phi) of current state
 void launch_init(lbm_ctx *ctx, const float *rho0, const float *u0);
 void launch_reduce(lbm_ctx *ctx, double *out);
@@ -101,5 +106,37 @@ void launch_get_populations(lbm_ctx *ctx, float *out);
 void launch_copy_mu(lbm_ctx *ctx, float *out);       // mu' + mu_ref
 void launch_set_populations(lbm_ctx *ctx, const float *in);
 const char *kernel_name(int id);
+
+// Counts a kernel launch of the context and, when per-kernel profiling is on,
+// brackets it with CUDA events on the context stream (events are recycled).
+struct TimedLaunch {
+  lbm_ctx *ctx;
+  ProfEvent ev;
+  TimedLaunch(lbm_ctx *c, int id) : ctx(c) {
+    ev.id = id;
+    if (ctx->prof_on) {
+      ev.start = take();
+      ev.stop = take();
+      cudaEventRecord(ev.start, ctx->stream);
+    }
+    ctx->launches++;
+  }
+  ~TimedLaunch() {
+    if (ctx->prof_on) {
+      cudaEventRecord(ev.stop, ctx->stream);
+      ctx->prof_pending.push_back(ev);
+    }
+  }
+  cudaEvent_t take() {
+    if (ctx->prof_free.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = ctx->prof_free.back();
+    ctx->prof_free.pop_back();
+    return e;
+  }
+};
 
 }  // namespace lbm

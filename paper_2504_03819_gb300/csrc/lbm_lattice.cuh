@@ -43,8 +43,16 @@ __device__ __forceinline__ float shift_rest(int q, float rb, float cb) {
   return fmaf(weight_of(q), rb, cb * iso_rest_of(q));
 }
 
+// Periodic index for v in [-n, 2n) (one period of wrap).
 __device__ __forceinline__ int wrap(int v, int n) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+// Periodic index for any v (tiles and halos of domains smaller than a tile
+// reach more than one period away).
+__device__ __forceinline__ int pmod(int v, int n) {
+  const int r = v % n;
+  return r < 0 ? r + n : r;
 }
 
 struct Node {

@@ -1,0 +1,471 @@
+// Fused time step (Sec. II B): three kernels per step instead of seven.
+//
+//   k_moments_v   rho, j from the populations (Eq. 11) + status check
+//   k_mu_z        mu' = mu0(rho) - mu_ref - kappa lap rho on fluid nodes
+//                 (Eqs. 2, 32), marching in z with the rho planes in shared
+//                 memory and the separable 27-point Laplacian
+//   k_fused       per (x, y) column tile, marching in z: F = (1/3 - rho) grad
+//                 mu, u = (j + F/2)/rho and phi = (p_m - rho/3) u on the tile
+//                 plus a one-node ring (shared-memory planes), Q_aa = -3
+//                 d_a phi_a (Eq. 27) on the tile, then the central-moment
+//                 collision (Eqs. 19-26, 28) and push streaming with halfway
+//                 bounce-back (Eq. 10, Sec. III C)
+//
+// The wetting kernels of lbm_forward.cu run between them when the domain has
+// solid nodes.  Everything is FP32; shared-memory rings hold the planes a
+// stencil needs so each field value is read from global memory about once.
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+namespace {
+
+// one-dimensional factor of the D3Q27 weights: w_q = w1(cx) w1(cy) w1(cz)
+__device__ __forceinline__ constexpr float w1(int c) { return c == 0 ? 2.0f / 3.0f : 1.0f / 6.0f; }
+
+// ---------------------------------------------------------------------------
+// moments (Eq. 11)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments_v(const T *__restrict__ f, const uint8_t *__restrict__ mask,
+                                                   const float *__restrict__ sb, float *__restrict__ rho,
+                                                   float *__restrict__ j, int *__restrict__ status, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad_nf = false, bad_dom = false;
+  if (n < kp.N && !(mask && mask[n])) {
+    const size_t N = (size_t)kp.N;
+    float v[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) v[q] = load_pop<T>(f + q * N + n);
+    // sums over the velocity components, grouped to keep FP32 rounding small
+    float s = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) s += v[q];
+#pragma unroll
+    for (int q = 0; q < 27; q += 3) sx += v[q + 2] - v[q];
+#pragma unroll
+    for (int g = 0; g < 3; ++g)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) sy += v[a + 6 + 9 * g] - v[a + 9 * g];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) sz += v[p + 18] - v[p];
+    const float r = s + (kp.shift_mode == LBM_SHIFT_REST ? sb[n] : kp.rho_shift);
+    rho[n] = r;
+    j[n] = sx;
+    j[N + n] = sy;
+    j[2 * N + n] = sz;
+    bad_nf = !(isfinite(r) && isfinite(sx) && isfinite(sy) && isfinite(sz));
+    bad_dom = !bad_nf && !(r > 0.0f && kp.b * r < 1.0f);
+  }
+  const unsigned nf = __ballot_sync(0xffffffffu, bad_nf), dm = __ballot_sync(0xffffffffu, bad_dom);
+  if ((threadIdx.x & 31) == 0) {
+    if (nf) atomicOr(status, STATUS_NONFINITE);
+    if (dm) atomicOr(status, STATUS_DOMAIN);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// chemical potential, z-marching (Eqs. 2, 32)
+// ---------------------------------------------------------------------------
+constexpr int MX = 32, MY = 8;   // tile of k_mu_z
+constexpr int MZ = 16;           // planes per block
+
+__global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, const uint8_t *__restrict__ mask,
+                                                 float *__restrict__ mu, KParams kp) {
+  constexpr int HX = MX + 2, HY = MY + 2, HP = HX * HY;
+  __shared__ float s_r[3][HP];
+  const int tx = threadIdx.x % MX, ty = threadIdx.x / MX;
+  const int x0 = blockIdx.x * MX, y0 = blockIdx.y * MY, z0 = blockIdx.z * MZ;
+  const int z1 = min(z0 + MZ, kp.nz);
+  const int nxy = kp.nx * kp.ny;
+  // xy offsets of this thread's halo-plane slots (periodic wrap), fixed over z
+  constexpr int SLOTS = (HP + MX * MY - 1) / (MX * MY);
+  int slot_xy[SLOTS];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int k = threadIdx.x + s * MX * MY;
+    const int hx = k % HX, hy = k / HX;
+    slot_xy[s] = k < HP ? pmod(x0 + hx - 1, kp.nx) + kp.nx * pmod(y0 + hy - 1, kp.ny) : 0;
+  }
+  // the next plane is fetched into registers one iteration ahead
+  float pre[SLOTS];
+  auto fetch_plane = [&](int z) {
+    const size_t zoff = (size_t)nxy * pmod(z, kp.nz);
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int k = threadIdx.x + s * MX * MY;
+      pre[s] = k < HP ? __ldg(rho + zoff + slot_xy[s]) : 0.0f;
+    }
+  };
+  auto store_plane = [&](int z) {
+    const int ring = (z + 3 * kp.nz + 3) % 3;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int k = threadIdx.x + s * MX * MY;
+      if (k < HP) s_r[ring][k] = pre[s];
+    }
+  };
+  auto load_plane = [&](int z) {
+    fetch_plane(z);
+    store_plane(z);
+  };
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < kp.nx && y < kp.ny;
+  // D(z') = sum_{cx,cy} w1 w1 (rho(x+cx, y+cy, z') - rho(x, y, z')) about
+  // each plane's own centre: small numbers, accurate in FP32
+  auto plane_sum = [&](int z, float &centre) {
+    const float *p = s_r[(z + 3 * kp.nz + 3) % 3];
+    const int c = (ty + 1) * HX + tx + 1;
+    centre = p[c];
+    const float row_m = w1(1) * (p[c - HX - 1] - centre) + w1(0) * (p[c - HX] - centre) + w1(1) * (p[c - HX + 1] - centre);
+    const float row_0 = w1(1) * (p[c - 1] - centre) + w1(1) * (p[c + 1] - centre);
+    const float row_p = w1(1) * (p[c + HX - 1] - centre) + w1(0) * (p[c + HX] - centre) + w1(1) * (p[c + HX + 1] - centre);
+    return w1(1) * row_m + w1(0) * row_0 + w1(1) * row_p;
+  };
+  load_plane(z0 - 1);
+  load_plane(z0);
+  fetch_plane(z0 + 1);
+  __syncthreads();
+  float dm, cm, d0, c0, dp, cp;
+  dm = plane_sum(z0 - 1, cm);
+  d0 = plane_sum(z0, c0);
+  for (int z = z0; z < z1; ++z) {
+    __syncthreads();  // the slot of plane z - 2 is free
+    store_plane(z + 1);
+    if (z + 1 < z1) fetch_plane(z + 2);
+    __syncthreads();
+    dp = plane_sum(z + 1, cp);
+    if (inside) {
+      const int n = x + kp.nx * y + nxy * z;
+      if (!(mask && mask[n])) {
+        // lap = 6 sum_q w_q (rho(x + c_q) - rho(x)), split by planes
+        const float lap = 6.0f * (w1(1) * (dm + (cm - c0)) + w1(0) * d0 + w1(1) * (dp + (cp - c0)));
+        mu[n] = mu0_vdw(c0, kp) - kp.kappa * lap;
+      }
+    }
+    dm = d0;
+    cm = c0;
+    d0 = dp;
+    c0 = cp;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused force / correction / collision / streaming
+// ---------------------------------------------------------------------------
+constexpr int TX = 32, TY = 8;  // column tile: one thread per (x, y)
+constexpr int NT = TX * TY;
+constexpr int H1X = TX + 2, H1Y = TY + 2, H1P = H1X * H1Y;  // one-node ring
+constexpr int H2X = TX + 4, H2Y = TY + 4, H2P = H2X * H2Y;  // two-node ring
+constexpr int S1 = (H1P + NT - 1) / NT;
+constexpr int S2 = (H2P + NT - 1) / NT;
+
+struct FusedSmem {
+  float mu[5][H2P];       // mu' planes z-2 .. z+2 (two-node ring)
+  float rho[4][H1P];      // rho planes z-2 .. z+1 (one-node ring)
+  float j[4][3][H1P];     // j planes
+  float phi[3][3][H1P];   // (p_m - rho/3) u planes z-1 .. z+1
+  float shift[3][4][H1P]; // storage shift by speed class, planes z-1 .. z+1
+  float uF[2][6][NT];     // u, F of the tile for planes z, z+1
+  uint8_t solid[4][H1P];  // mask planes
+};
+
+__device__ __forceinline__ int r5(int z) { return (z + 10) % 5; }  // z >= -2
+__device__ __forceinline__ int r4(int z) { return (z + 8) & 3; }
+__device__ __forceinline__ int r3(int z) { return (z + 6) % 3; }
+__device__ __forceinline__ int r2(int z) { return (z + 4) & 1; }
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) k_fused(const T *__restrict__ fin, T *__restrict__ fout,
+                                                 const uint8_t *__restrict__ mask, const float *__restrict__ rho,
+                                                 const float *__restrict__ jv, const float *__restrict__ mu,
+                                                 float *__restrict__ sb, KParams kp, int TZ) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int z1 = min(z0 + TZ, kp.nz);
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+  const int nxy = nx * ny;
+  const size_t N = (size_t)kp.N;
+  const bool rest = kp.shift_mode == LBM_SHIFT_REST;
+
+  // xy offsets (periodic) of this thread's slots in the two-node and the
+  // one-node rings; fixed for the whole column
+  int xy2[S2], xy1[S1];
+#pragma unroll
+  for (int s = 0; s < S2; ++s) {
+    const int k = tid + s * NT;
+    xy2[s] = k < H2P ? pmod(x0 + k % H2X - 2, nx) + nx * pmod(y0 + k / H2X - 2, ny) : 0;
+  }
+#pragma unroll
+  for (int s = 0; s < S1; ++s) {
+    const int k = tid + s * NT;
+    xy1[s] = k < H1P ? pmod(x0 + k % H1X - 1, nx) + nx * pmod(y0 + k / H1X - 1, ny) : 0;
+  }
+  auto zoff = [&](int z) { return (size_t)nxy * pmod(z, nz); };
+
+  // planes are fetched into registers one iteration before they are stored
+  // to shared memory, so their DRAM latency overlaps a whole plane of work
+  float pmu[S2], prho[S1], pj[3][S1];
+  uint8_t psolid[S1];
+  auto fetch = [&](int zm, int zr) {  // mu' plane zm, rho/j/mask plane zr
+    const size_t om = zoff(zm), orr = zoff(zr);
+#pragma unroll
+    for (int s = 0; s < S2; ++s) pmu[s] = (tid + s * NT < H2P) ? __ldg(mu + om + xy2[s]) : 0.0f;
+#pragma unroll
+    for (int s = 0; s < S1; ++s) {
+      const bool ok = tid + s * NT < H1P;
+      const size_t g = orr + xy1[s];
+      prho[s] = ok ? __ldg(rho + g) : 0.0f;
+      pj[0][s] = ok ? __ldg(jv + g) : 0.0f;
+      pj[1][s] = ok ? __ldg(jv + N + g) : 0.0f;
+      pj[2][s] = ok ? __ldg(jv + 2 * N + g) : 0.0f;
+      psolid[s] = (ok && mask) ? mask[g] : (uint8_t)0;
+    }
+  };
+  auto store = [&](int zm, int zr) {
+    float *dm = S.mu[r5(zm)];
+#pragma unroll
+    for (int s = 0; s < S2; ++s)
+      if (tid + s * NT < H2P) dm[tid + s * NT] = pmu[s];
+    const int rg = r4(zr);
+#pragma unroll
+    for (int s = 0; s < S1; ++s) {
+      const int k = tid + s * NT;
+      if (k < H1P) {
+        S.rho[rg][k] = prho[s];
+        S.j[rg][0][k] = pj[0][s];
+        S.j[rg][1][k] = pj[1][s];
+        S.j[rg][2][k] = pj[2][s];
+        S.solid[rg][k] = psolid[s];
+      }
+    }
+  };
+  // F, u, phi at every one-node-ring position of plane z (u, F kept for the
+  // tile positions)
+  auto fields = [&](int z, bool keep_uF) {
+    const int rg = r4(z), rp = r3(z);
+    const float *m0 = S.mu[r5(z - 1)], *m1 = S.mu[r5(z)], *m2 = S.mu[r5(z + 1)];
+    for (int k = tid; k < H1P; k += NT) {
+      const int hx = k % H1X, hy = k / H1X;
+      float phx = 0.0f, phy = 0.0f, phz = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f, Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+      float sh0 = 0.0f, sh1 = 0.0f, sh2 = 0.0f, sh3 = 0.0f;
+      if (!S.solid[rg][k]) {
+        const int c = (hy + 1) * H2X + hx + 1;  // position in the two-node ring
+        const float mc = m1[c];
+        // sum_q w_q c_q mu'(x + c_q): sum_q w_q c_q = 0 makes the centre term
+        // drop out, and mu' is a small deviation, so no centring is needed
+        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+          if (q == 13) continue;
+          const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
+          const float *pl = cz < 0 ? m0 : (cz == 0 ? m1 : m2);
+          const float v = pl[c + cx + cy * H2X];
+          if (cx) gx = fmaf(cx * weight_of(q), v, gx);
+          if (cy) gy = fmaf(cy * weight_of(q), v, gy);
+          if (cz) gz = fmaf(cz * weight_of(q), v, gz);
+        }
+        const float r = S.rho[rg][k];
+        const float cf = 3.0f * (1.0f / 3.0f - r);
+        Fx = cf * gx;
+        Fy = cf * gy;
+        Fz = cf * gz;
+        const float ir = 1.0f / r;
+        ux = (S.j[rg][0][k] + 0.5f * Fx) * ir;
+        uy = (S.j[rg][1][k] + 0.5f * Fy) * ir;
+        uz = (S.j[rg][2][k] + 0.5f * Fz) * ir;
+        const float e = basis_c(r, mc, kp);
+        phx = e * ux;
+        phy = e * uy;
+        phz = e * uz;
+        if (rest) {  // destination-keyed shifts of the four speed classes
+          sh0 = shift_rest(13, r, e);
+          sh1 = shift_rest(12, r, e);
+          sh2 = shift_rest(9, r, e);
+          sh3 = shift_rest(0, r, e);
+        }
+      }
+      S.phi[rp][0][k] = phx;
+      S.phi[rp][1][k] = phy;
+      S.phi[rp][2][k] = phz;
+      if (rest) {
+        S.shift[rp][0][k] = sh0;
+        S.shift[rp][1][k] = sh1;
+        S.shift[rp][2][k] = sh2;
+        S.shift[rp][3][k] = sh3;
+      }
+      if (keep_uF && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
+        const int t = (hy - 1) * TX + hx - 1;
+        float *o = S.uF[r2(z)][0];
+        o[t] = ux;
+        o[NT + t] = uy;
+        o[2 * NT + t] = uz;
+        o[3 * NT + t] = Fx;
+        o[4 * NT + t] = Fy;
+        o[5 * NT + t] = Fz;
+      }
+    }
+  };
+
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < nx && y < ny;
+  // destination offsets in the node index for c = -1, 0, +1 per axis
+  const int ox[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? -(nx - 1) : 1};
+  const int oy[3] = {y == 0 ? (ny - 1) * nx : -nx, 0, y == ny - 1 ? -(ny - 1) * nx : nx};
+
+  // prologue: mu' planes z0-2 .. z0+1 and rho/j planes z0-1 .. z0 in shared
+  // memory, mu'(z0+2) and rho/j(z0+1) in registers; phi of z0-1 and z0,
+  // u/F of z0
+  fetch(z0 - 2, z0 - 1);
+  store(z0 - 2, z0 - 1);
+  fetch(z0 - 1, z0);
+  store(z0 - 1, z0);
+  fetch(z0, z0);
+  store(z0, z0);
+  fetch(z0 + 1, z0);
+  store(z0 + 1, z0);
+  fetch(z0 + 2, z0 + 1);
+  __syncthreads();
+  fields(z0 - 1, false);
+  fields(z0, true);
+
+  for (int z = z0; z < z1; ++z) {
+    // publish mu'(z+2), rho/j(z+1); prefetch mu'(z+3), rho/j(z+2)
+    store(z + 2, z + 1);
+    if (z + 1 < z1) fetch(z + 3, z + 2);
+    // populations of this node
+    const int n = x + nx * y + nxy * z;
+    const bool active = inside && !(S.solid[r4(z)][(ty + 1) * H1X + tx + 1]);
+    float f[27];
+    float rb = kp.rho_shift, cb = 0.0f;
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < 27; ++q) f[q] = load_pop<T>(fin + q * N + n);
+      if (rest) {
+        rb = sb[n];
+        cb = sb[N + n];
+      }
+    }
+    __syncthreads();
+    fields(z + 1, true);
+    __syncthreads();
+    if (!active) continue;
+
+    // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa (phi_a(x + c_q) - phi_a(x))
+    const int c1 = (ty + 1) * H1X + tx + 1;
+    const float *p0 = S.phi[r3(z - 1)][0], *p1 = S.phi[r3(z)][0], *p2 = S.phi[r3(z + 1)][0];
+    float Qx = 0.0f, Qy = 0.0f, Qz = 0.0f;
+    {
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        if (q == 13) continue;
+        const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
+        const float *pl = cz < 0 ? p0 : (cz == 0 ? p1 : p2);
+        const int o = c1 + cx + cy * H1X;
+        if (cx) Qx = fmaf(cx * weight_of(q), pl[o], Qx);
+        if (cy) Qy = fmaf(cy * weight_of(q), pl[H1P + o], Qy);
+        if (cz) Qz = fmaf(cz * weight_of(q), pl[2 * H1P + o], Qz);
+      }
+      Qx *= -9.0f;
+      Qy *= -9.0f;
+      Qz *= -9.0f;
+    }
+    const float *uF = S.uF[r2(z)][0];
+    const int t = ty * TX + tx;
+    const float ux = uF[t], uy = uF[NT + t], uz = uF[2 * NT + t];
+    const float Fx = uF[3 * NT + t], Fy = uF[4 * NT + t], Fz = uF[5 * NT + t];
+    const float r_own = S.rho[r4(z)][c1];
+    const float mu_own = S.mu[r5(z)][(ty + 2) * H2X + tx + 2];
+    const float pm = pm_of(mu_own, kp);
+    float om1 = kp.om[1];
+    if (kp.nu > 0.0f) om1 = 1.0f / (r_own * kp.nu / pm + 0.5f);
+
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] += rest ? shift_rest(q, rb, cb) : weight_of(q) * kp.rho_shift;
+    to_central(f, ux, uy, uz);
+    collide_cm(f, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
+    from_central(f, ux, uy, uz);
+
+    // push with bounce-back; shifts keyed by the destination's fields
+    const int oz[3] = {z == 0 ? (nz - 1) * nxy : -nxy, 0, z == nz - 1 ? -(nz - 1) * nxy : nxy};
+    const float c_own = rest ? basis_c(r_own, mu_own, kp) : 0.0f;
+    const bool has_mask = mask != nullptr;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
+      float sh = weight_of(q) * kp.rho_shift;
+      if (q == 13) {
+        if (rest) sh = shift_rest(q, r_own, c_own);
+        store_pop<T>(fout + q * N + n, f[q] - sh);
+        continue;
+      }
+      const int hk = c1 + cx + cy * H1X;
+      const int rg = r4(z + cz);
+      if (has_mask && S.solid[rg][hk]) {
+        if (rest) sh = shift_rest(q, r_own, c_own);
+        store_pop<T>(fout + (size_t)(26 - q) * N + n, f[q] - sh);
+      } else {
+        if (rest) sh = S.shift[r3(z + cz)][cx * cx + cy * cy + cz * cz][hk];
+        const int m = n + ox[cx + 1] + oy[cy + 1] + oz[cz + 1];
+        store_pop<T>(fout + q * N + m, f[q] - sh);
+      }
+    }
+    if (rest) {
+      sb[n] = r_own;
+      sb[N + n] = c_own;
+    }
+  }
+}
+
+constexpr int FUSED_TZ = 16;
+
+}  // namespace
+
+size_t fused_smem_bytes() { return sizeof(FusedSmem); }
+
+void launch_step_fused(lbm_ctx *ctx) {
+  const KParams &kp = ctx->kp;
+  const Fields &d = ctx->fld;
+  cudaStream_t s = ctx->stream;
+  const int g = (kp.N + 255) / 256;
+  const void *fin = ctx->f[ctx->cur];
+  void *fout = ctx->f[1 - ctx->cur];
+  {
+    TimedLaunch t(ctx, K_MOMENTS);
+    if (ctx->storage == LBM_F16)
+      k_moments_v<__half><<<g, 256, 0, s>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
+    else
+      k_moments_v<float><<<g, 256, 0, s>>>((const float *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
+  }
+  if (ctx->n_bnd) launch_wet_rho(ctx);
+  {
+    TimedLaunch t(ctx, K_MU);
+    dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + MZ - 1) / MZ);
+    k_mu_z<<<grid, MX * MY, 0, s>>>(d.rho, ctx->mask, d.mu, kp);
+  }
+  if (ctx->n_bnd) launch_wet_mu(ctx);
+  {
+    TimedLaunch t(ctx, K_COLLIDE);
+    dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + FUSED_TZ - 1) / FUSED_TZ);
+    const size_t sm = sizeof(FusedSmem);
+    static bool attr_set = false;  // the attribute is per function, set once per process
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_fused<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr_set = true;
+    }
+    if (ctx->storage == LBM_F16) {
+      k_fused<__half><<<grid, NT, sm, s>>>((const __half *)fin, (__half *)fout, ctx->mask, d.rho, d.j, d.mu, d.sb,
+                                           kp, FUSED_TZ);
+    } else {
+      k_fused<float><<<grid, NT, sm, s>>>((const float *)fin, (float *)fout, ctx->mask, d.rho, d.j, d.mu, d.sb,
+                                          kp, FUSED_TZ);
+    }
+  }
+  ctx->cur = 1 - ctx->cur;
+}
+
+}  // namespace lbm
