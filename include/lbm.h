@@ -192,6 +192,59 @@ const char *lbm_last_error(const lbm_ctx *ctx);
 /* Free the host-side context (no device memory is owned). */
 void lbm_destroy(lbm_ctx *ctx);
 
+/* ---- discrete adjoint ---------------------------------------------------
+ *
+ * The paper has no adjoint; these entry points give the exact reverse-mode
+ * derivative of the discrete step above (the transpose of its linearisation
+ * at the given state), so that gradients of a scalar objective J of the
+ * state after T steps can be taken with respect to the parameters and the
+ * initial density.  Adjoint fields lambda = dJ/df are unshifted FP32 arrays
+ * of 27*N floats (population layout as above), zero on solid nodes.
+ * Parameter gradients are LBM_NGRAD doubles in the order
+ * [kappa, omega_0 .. omega_10, wetting_value], summed in FP64 in a fixed
+ * order and ADDED to the caller's device array.  Derivatives through the
+ * contact-line band test and limiter (Eq. 38) are those of the branch taken
+ * at the given state (a clamped density passes no gradient).
+ */
+#define LBM_NGRAD 13
+
+/* Objectives (of the current state), J[0] = value:
+ *  LBM_OBJ_ENERGY          1/2 sum_fluid rho |u|^2 (u force-corrected, Eq. 11)
+ *  LBM_OBJ_CENTROID_X      sum x (rho - rho_v) / sum (rho - rho_v), fluid nodes
+ *                          (J[1] = the denominator)
+ *  LBM_OBJ_CONTACT_RADIUS  sqrt(A/pi), A = sum over the fluid layer z = wall_z+1
+ *                          of (rho - rho_v)/(rho_l - rho_v)
+ */
+enum { LBM_OBJ_ENERGY = 0, LBM_OBJ_CENTROID_X = 1, LBM_OBJ_CONTACT_RADIUS = 2 };
+
+/* Value of objective `kind` of the current state into J (device, 2 doubles)
+ * and its seed lambda = dJ/df into lam (device, 27*N floats, overwritten).
+ * grad_params (device, LBM_NGRAD doubles, or NULL) receives the objective's
+ * direct dependence on the parameters at fixed populations (the kinetic
+ * energy depends on kappa and the wetting value through F), accumulated. */
+int lbm_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad_params);
+
+/*
+ * One adjoint step.  state_t: raw state at time t (lbm_state_bytes bytes,
+ * device, as from lbm_get_state); lam_next: dJ/df(t+1) (device, 27*N
+ * floats); lam_t: output dJ/df(t) (device, 27*N floats, must not alias
+ * lam_next); grad_params: device, LBM_NGRAD doubles, accumulated.  The
+ * context's current state becomes state_t (the forward fields of f(t) are
+ * recomputed from it).  Enqueues only.
+ */
+int lbm_adjoint_step(lbm_ctx *ctx, const void *state_t, const float *lam_next, float *lam_t,
+                     double *grad_params);
+
+/*
+ * Adjoint of lbm_set_state: given lam0 = dJ/df(0) (device, 27*N floats),
+ * writes dJ/drho0 into grad_rho0 (device, N floats, 0 on solid nodes) and
+ * adds the parameter contributions of the initialisation (kappa, wetting
+ * value) to grad_params.  rho0, u0 as passed to lbm_set_state (u0 may be
+ * NULL).  The context's current state becomes the initial state of rho0, u0.
+ */
+int lbm_adjoint_init(lbm_ctx *ctx, const float *rho0, const float *u0, const float *lam0,
+                     double *grad_params, float *grad_rho0);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Number of kernels this context has launched since init. */

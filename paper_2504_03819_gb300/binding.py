@@ -18,6 +18,8 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_NONFINITE, LBM_ERR_DOM
 LBM_F32, LBM_F16 = 0, 1
 SHIFT_CONST, SHIFT_REST = 0, 1
 WET_NEUTRAL, WET_PHI, WET_DELTA = 0, 1, 2
+OBJ_ENERGY, OBJ_CENTROID_X, OBJ_CONTACT_RADIUS = 0, 1, 2
+NGRAD = 13   # [kappa, omega_0 .. omega_10, wetting_value]
 ERROR_NAMES = {LBM_ERR_ARG: "LBM_ERR_ARG", LBM_ERR_CUDA: "LBM_ERR_CUDA", LBM_ERR_STATE: "LBM_ERR_STATE",
                LBM_ERR_NONFINITE: "LBM_ERR_NONFINITE", LBM_ERR_DOMAIN: "LBM_ERR_DOMAIN",
                LBM_ERR_SIZE: "LBM_ERR_SIZE"}
@@ -37,6 +39,9 @@ SIGNATURES = {
     "lbm_set_raw_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_objective": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_adjoint_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_adjoint_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_destroy": (None, [C.c_void_p]),
     "lbm_launch_count": (C.c_longlong, [C.c_void_p]),
@@ -265,6 +270,42 @@ class Domain:
         f = self._dev(f, (27, self.nz, self.ny, self.nx))
         self._check(self.lib.lbm_set_populations(self.ctx, _ptr(f)), "lbm_set_populations")
         self.stream.synchronize()
+
+    # -- discrete adjoint -------------------------------------------------------
+    def objective(self, kind: int, wall_z: int = 0, grad=None):
+        """(J, dJ/df) of the current state; J is a CUDA float64 tensor (2,).
+        The objective's direct parameter dependence is added to grad if given."""
+        t = self.torch
+        J = t.zeros(2, dtype=t.float64, device=self.device)
+        lam = t.empty((27, self.nz, self.ny, self.nx), dtype=t.float32, device=self.device)
+        self._check(self.lib.lbm_objective(self.ctx, int(kind), int(wall_z), _ptr(J), _ptr(lam), _ptr(grad)),
+                    "lbm_objective")
+        return J, lam
+
+    def adjoint_step(self, state_t, lam_next, grad, lam_out=None):
+        """dJ/df(t) from dJ/df(t+1) at the raw state of time t; adds the
+        parameter gradients to grad (CUDA float64, NGRAD)."""
+        t = self.torch
+        lam_next = self._dev(lam_next, (27, self.nz, self.ny, self.nx))
+        out = lam_out if lam_out is not None else t.empty_like(lam_next)
+        raw = state_t.to(device=self.device, dtype=t.uint8).contiguous()
+        assert raw.numel() == self.state_bytes() and grad.dtype == t.float64 and grad.numel() == NGRAD
+        self._check(self.lib.lbm_adjoint_step(self.ctx, _ptr(raw), _ptr(lam_next), _ptr(out), _ptr(grad)),
+                    "lbm_adjoint_step")
+        return out
+
+    def adjoint_init(self, rho0, u0, lam0, grad):
+        """dJ/drho0 from dJ/df(0); adds the initialisation's parameter
+        gradients to grad.  Leaves the initial state of rho0, u0 current."""
+        t = self.torch
+        shp = (self.nz, self.ny, self.nx)
+        r = self._dev(rho0, shp)
+        u = None if u0 is None else self._dev(u0, (3,) + shp)
+        lam0 = self._dev(lam0, (27,) + shp)
+        g = t.empty(shp, dtype=t.float32, device=self.device)
+        self._check(self.lib.lbm_adjoint_init(self.ctx, _ptr(r), _ptr(u), _ptr(lam0), _ptr(grad), _ptr(g)),
+                    "lbm_adjoint_init")
+        return g
 
     def launch_count(self) -> int:
         return int(self.lib.lbm_launch_count(self.ctx))

@@ -1,0 +1,841 @@
+// Discrete adjoint of one time step (reverse mode of the step in
+// lbm_forward.cu / lbm_step_fused.cu).  The paper has no adjoint; this is the
+// exact transpose of the linearised discrete map f(t) -> f(t+1).
+//
+// Given the state f(t) and lambda(t+1) = dJ/df(t+1), the kernels compute
+// lambda(t) = (df(t+1)/df(t))^T lambda(t+1) and add the step's contribution
+// to dJ/d{kappa, omega_0..10, wetting value}:
+//
+//   forward recompute   rho, j, mu', u, F, phi, Q of f(t) (staged kernels)
+//   k_adj_collide       pull of lambda(t+1) (transpose of push + bounce-back),
+//                       transpose of the inverse CM transform, of the
+//                       collision (Eqs. 21-26, 28) and of the forward CM
+//                       transform (Eq. 19), with the u-derivatives of both
+//                       transforms; adjoint sources for u, F, Q, p_m, omega_1
+//   k_adj_phi           Q_aa = -3 d_a phi_a (Eq. 27) transposed
+//   k_adj_fields        phi = (p_m - rho/3) u, u = (j + F/2)/rho,
+//                       F = (1/3 - rho) grad mu (Eq. 12), p_m = (1 + mu)/3,
+//                       per-node omega_1 (Sec. II B) transposed
+//   k_adj_mu            grad mu transposed (a gather) + the local p_m term
+//   k_adj_wet_mu        Eq. 36 transposed (solid -> fluid neighbours)
+//   k_adj_rho           mu = mu0(rho) - kappa lap rho (Eqs. 2, 32) transposed
+//   k_adj_wet_prep /    Eqs. 37-38 transposed (branch of the forward pass:
+//   k_adj_wet_rho       clamped densities pass no gradient)
+//   k_adj_out           lambda_q(t) = local part + lambda_rho + c_q . lambda_j
+//
+// Parameter gradients are summed per block in FP64 and reduced in a fixed
+// order (deterministic).
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int BLK = 128;
+// parameter slots: 0 kappa, 1..11 omega_0..omega_10, 12 wetting value
+constexpr int NPAR = 13;
+
+// ---------------------------------------------------------------------------
+// one axis of the CM transform: forward A(u), inverse B(u) and transposes
+// ---------------------------------------------------------------------------
+// forward: M0 = a+b+c, M1 = (c-a) - u M0, M2 = (a+c) - 2u(c-a) + u^2 M0
+__device__ __forceinline__ void fwd_T(float &a, float &b, float &c, float u) {
+  // (a, b, c) <- A(u)^T (l0, l1, l2) with (l0, l1, l2) = (a, b, c) on entry
+  const float l0 = a, l1 = b, l2 = c;
+  a = l0 + (-1.0f - u) * l1 + (1.0f + u) * (1.0f + u) * l2;
+  b = l0 - u * l1 + u * u * l2;
+  c = l0 + (1.0f - u) * l1 + (1.0f - u) * (1.0f - u) * l2;
+}
+// d/du of the forward outputs given the inputs (a, b, c), dotted with the
+// adjoints (l1, l2) of (M1, M2)
+__device__ __forceinline__ float fwd_du(float a, float b, float c, float u, float l1, float l2) {
+  const float m0 = a + b + c, d = c - a;
+  return -m0 * l1 + (-2.0f * d + 2.0f * u * m0) * l2;
+}
+// inverse: a = ((u^2-u) M0 + (2u-1) M1 + M2)/2, b = (1-u^2) M0 - 2u M1 - M2,
+//          c = ((u^2+u) M0 + (2u+1) M1 + M2)/2
+__device__ __forceinline__ void inv_T(float &m0, float &m1, float &m2, float u) {
+  const float la = m0, lb = m1, lc = m2;
+  m0 = 0.5f * (u * u - u) * la + (1.0f - u * u) * lb + 0.5f * (u * u + u) * lc;
+  m1 = 0.5f * (2.0f * u - 1.0f) * la - 2.0f * u * lb + 0.5f * (2.0f * u + 1.0f) * lc;
+  m2 = 0.5f * la - lb + 0.5f * lc;
+}
+__device__ __forceinline__ float inv_du(float m0, float m1, float la, float lb, float lc, float u) {
+  return la * (0.5f * (2.0f * u - 1.0f) * m0 + m1) + lb * (-2.0f * u * m0 - 2.0f * m1) +
+         lc * (0.5f * (2.0f * u + 1.0f) * m0 + m1);
+}
+
+// copy helpers for 27-arrays
+__device__ __forceinline__ void cp27(float *d, const float *s) {
+#pragma unroll
+  for (int q = 0; q < 27; ++q) d[q] = s[q];
+}
+
+// pass indices (same order as to_central / from_central)
+// z-pass triples: (p, p+9, p+18), p = 0..8;  y-pass: (a+9g, a+3+9g, a+6+9g);
+// x-pass: (q, q+1, q+2), q = 0, 3, ..., 24.
+
+// lam <- (d from_central / d k)^T lam, accumulating d/du into gu.  kin are the
+// post-collision moments (input of from_central).
+__device__ __forceinline__ void from_central_vjp(float lam[27], const float kin[27], float ux, float uy, float uz,
+                                                 float &gux, float &guy, float &guz) {
+  // stage values: K0 = kin, K1 = after x-pass, K2 = after y-pass
+  float K1[27], K2[27];
+  cp27(K1, kin);
+#pragma unroll
+  for (int q = 0; q < 27; q += 3) cm_axis_inv(K1[q], K1[q + 1], K1[q + 2], ux);
+  cp27(K2, K1);
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cm_axis_inv(K2[a + 9 * g], K2[a + 3 + 9 * g], K2[a + 6 + 9 * g], uy);
+  // z-pass (last) transposed, inputs K2
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    guz += inv_du(K2[p], K2[p + 9], lam[p], lam[p + 9], lam[p + 18], uz);
+    inv_T(lam[p], lam[p + 9], lam[p + 18], uz);
+  }
+  // y-pass transposed, inputs K1
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int i0 = a + 9 * g, i1 = a + 3 + 9 * g, i2 = a + 6 + 9 * g;
+      guy += inv_du(K1[i0], K1[i1], lam[i0], lam[i1], lam[i2], uy);
+      inv_T(lam[i0], lam[i1], lam[i2], uy);
+    }
+  // x-pass transposed, inputs K0 = kin
+#pragma unroll
+  for (int q = 0; q < 27; q += 3) {
+    gux += inv_du(kin[q], kin[q + 1], lam[q], lam[q + 1], lam[q + 2], ux);
+    inv_T(lam[q], lam[q + 1], lam[q + 2], ux);
+  }
+}
+
+// lam <- (d to_central / d f)^T lam, accumulating d/du.  f are the populations
+// (input of to_central).
+__device__ __forceinline__ void to_central_vjp(float lam[27], const float f[27], float ux, float uy, float uz,
+                                               float &gux, float &guy, float &guz) {
+  // stage values: G0 = f, G1 = after z-pass, G2 = after y-pass
+  float G1[27], G2[27];
+  cp27(G1, f);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) cm_axis(G1[p], G1[p + 9], G1[p + 18], uz);
+  cp27(G2, G1);
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cm_axis(G2[a + 9 * g], G2[a + 3 + 9 * g], G2[a + 6 + 9 * g], uy);
+  // x-pass (last) transposed, inputs G2
+#pragma unroll
+  for (int q = 0; q < 27; q += 3) {
+    gux += fwd_du(G2[q], G2[q + 1], G2[q + 2], ux, lam[q + 1], lam[q + 2]);
+    fwd_T(lam[q], lam[q + 1], lam[q + 2], ux);
+  }
+  // y-pass transposed, inputs G1
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int i0 = a + 9 * g, i1 = a + 3 + 9 * g, i2 = a + 6 + 9 * g;
+      guy += fwd_du(G1[i0], G1[i1], G1[i2], uy, lam[i1], lam[i2]);
+      fwd_T(lam[i0], lam[i1], lam[i2], uy);
+    }
+  // z-pass transposed, inputs f
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    guz += fwd_du(f[p], f[p + 9], f[p + 18], uz, lam[p + 9], lam[p + 18]);
+    fwd_T(lam[p], lam[p + 9], lam[p + 18], uz);
+  }
+}
+
+#define LK(a, b, c) lk[(a) + 3 * (b) + 9 * (c)]
+#define LS(a, b, c) ls[(a) + 3 * (b) + 9 * (c)]
+
+// Transpose of collide_cm (Eqs. 21-26, 28).  k: pre-collision moments;
+// ls: adjoint of the post-collision moments (consumed); lk: adjoint of k
+// (output).  Accumulates the adjoints of p_m, F, Q, omega_1 (om1) and of
+// the global rates (gom[0..10], gom[1] unused here).
+__device__ __forceinline__ void collide_vjp(const float *k, float *ls, float *lk, float pm, float Fx, float Fy,
+                                            float Fz, float Qx, float Qy, float Qz, float om1, const KParams &kp,
+                                            float &lpm, float &lFx, float &lFy, float &lFz, float &lQx, float &lQy,
+                                            float &lQz, float &lom1, float gom[11]) {
+  const float o0 = kp.om[0], o2 = kp.om[2], o3 = kp.om[3], o4 = kp.om[4], o5 = kp.om[5];
+  const float o6 = kp.om[6], o7 = kp.om[7], o8 = kp.om[8], o9 = kp.om[9], o10 = kp.om[10];
+  const float cs2 = 1.0f / 3.0f;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) lk[q] = 0.0f;
+  LK(0, 0, 0) = LS(0, 0, 0);
+  // first order
+  {
+    const float Fa[3] = {Fx, Fy, Fz};
+    const int ids[3] = {1, 3, 9};
+    float *lF[3] = {&lFx, &lFy, &lFz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float l = ls[ids[a]];
+      lk[ids[a]] = (1.0f - o0) * l;
+      *lF[a] += (1.0f - 0.5f * o0) * l;
+      gom[0] += (-k[ids[a]] - 0.5f * Fa[a]) * l;
+    }
+  }
+  // second order off-diagonal
+  {
+    const int ids[3] = {4, 12, 10};  // k110, k011, k101
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lk[ids[a]] = (1.0f - om1) * ls[ids[a]];
+      lom1 += -k[ids[a]] * ls[ids[a]];
+    }
+  }
+  // second order diagonal
+  {
+    const float l200 = LS(2, 0, 0), l020 = LS(0, 2, 0), l002 = LS(0, 0, 2);
+    const float lS = (l200 + l020 + l002) * (1.0f / 3.0f);
+    const float lA = (l200 - 2.0f * l020 + l002) * (1.0f / 3.0f);
+    const float lB = (l200 + l020 - 2.0f * l002) * (1.0f / 3.0f);
+    const float k200 = k[2], k020 = k[6], k002 = k[18];
+    LK(2, 0, 0) += (1.0f - om1) * (lA + lB) + (1.0f - o2) * lS;
+    LK(0, 2, 0) += -(1.0f - om1) * lA + (1.0f - o2) * lS;
+    LK(0, 0, 2) += -(1.0f - om1) * lB + (1.0f - o2) * lS;
+    const float h1 = 1.0f - 0.5f * om1, h2 = 1.0f - 0.5f * o2;
+    lQx += h1 * (lA + lB) + h2 * lS;
+    lQy += -h1 * lA + h2 * lS;
+    lQz += -h1 * lB + h2 * lS;
+    lpm += 3.0f * o2 * lS;
+    lom1 += (-(k200 - k020) - 0.5f * (Qx - Qy)) * lA + (-(k200 - k002) - 0.5f * (Qx - Qz)) * lB;
+    gom[2] += (-(k200 + k020 + k002) + 3.0f * pm - 0.5f * (Qx + Qy + Qz)) * lS;
+  }
+  // third order
+  {
+    // pairs (k120, k102) with F_x, (k210, k012) with F_y, (k201, k021) with F_z
+    const int P0[3] = {7, 5, 11}, P1[3] = {19, 21, 15};
+    const float Fa[3] = {Fx, Fy, Fz};
+    float *lF[3] = {&lFx, &lFy, &lFz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float lP = 0.5f * (ls[P0[a]] + ls[P1[a]]);
+      const float lD = 0.5f * (ls[P0[a]] - ls[P1[a]]);
+      lk[P0[a]] = (1.0f - o3) * lP + (1.0f - o4) * lD;
+      lk[P1[a]] = (1.0f - o3) * lP - (1.0f - o4) * lD;
+      *lF[a] += 2.0f * (1.0f - 0.5f * o3) * cs2 * lP;
+      gom[3] += (-(k[P0[a]] + k[P1[a]]) - Fa[a] * cs2) * lP;
+      gom[4] += -(k[P0[a]] - k[P1[a]]) * lD;
+    }
+    LK(1, 1, 1) = (1.0f - o5) * LS(1, 1, 1);
+    gom[5] += -KM(1, 1, 1) * LS(1, 1, 1);
+  }
+  // fourth order
+  {
+    const float a = KM(2, 2, 0), b = KM(2, 0, 2), c = KM(0, 2, 2);
+    const float lT = (LS(2, 2, 0) + LS(2, 0, 2) + LS(0, 2, 2)) * (1.0f / 3.0f);
+    const float lD1 = (LS(2, 2, 0) - LS(2, 0, 2)) * (1.0f / 3.0f);
+    const float lD2 = (LS(2, 2, 0) - LS(0, 2, 2)) * (1.0f / 3.0f);
+    LK(2, 2, 0) = (1.0f - o6) * (lD1 + lD2) + (1.0f - o7) * lT;
+    LK(2, 0, 2) = (1.0f - o6) * (-2.0f * lD1 + lD2) + (1.0f - o7) * lT;
+    LK(0, 2, 2) = (1.0f - o6) * (lD1 - 2.0f * lD2) + (1.0f - o7) * lT;
+    float Q220 = 0.0f, Q202 = 0.0f, Q022 = 0.0f;
+    if (kp.q4) {
+      Q220 = (Qx + Qy) * cs2;
+      Q202 = (Qx + Qz) * cs2;
+      Q022 = (Qy + Qz) * cs2;
+      const float h6 = 1.0f - 0.5f * o6, h7 = 1.0f - 0.5f * o7;
+      const float l220 = h6 * (lD1 + lD2) + h7 * lT;
+      const float l202 = h6 * (-2.0f * lD1 + lD2) + h7 * lT;
+      const float l022 = h6 * (lD1 - 2.0f * lD2) + h7 * lT;
+      lQx += (l220 + l202) * cs2;
+      lQy += (l220 + l022) * cs2;
+      lQz += (l202 + l022) * cs2;
+    }
+    lpm += o7 * lT;
+    gom[6] += (-(a - 2.0f * b + c) - 0.5f * (Q220 - 2.0f * Q202 + Q022)) * lD1 +
+              (-(a + b - 2.0f * c) - 0.5f * (Q220 + Q202 - 2.0f * Q022)) * lD2;
+    gom[7] += (-(a + b + c) + pm - 0.5f * (Q220 + Q202 + Q022)) * lT;
+    const int ids[3] = {14, 16, 22};  // k211, k121, k112
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lk[ids[i]] = (1.0f - o8) * ls[ids[i]];
+      gom[8] += -k[ids[i]] * ls[ids[i]];
+    }
+  }
+  // fifth order
+  {
+    const int i122 = 1 + 6 + 18, i212 = 2 + 3 + 18, i221 = 2 + 6 + 9;
+    const int id5[3] = {i122, i212, i221};
+    const float Fa[3] = {Fx, Fy, Fz};
+    float *lF[3] = {&lFx, &lFy, &lFz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float l = ls[id5[a]];
+      lk[id5[a]] = (1.0f - o9) * l;
+      *lF[a] += (1.0f - 0.5f * o9) * cs2 * cs2 * l;
+      gom[9] += (-k[id5[a]] - 0.5f * Fa[a] * cs2 * cs2) * l;
+    }
+  }
+  // sixth order
+  LK(2, 2, 2) = (1.0f - o10) * LS(2, 2, 2);
+  lpm += o10 * cs2 * cs2 * LS(2, 2, 2);
+  gom[10] += (-KM(2, 2, 2) + pm * cs2 * cs2) * LS(2, 2, 2);
+}
+
+// block sum of NPAR floats (as doubles) into partial[blockIdx.x * NPAR + i]
+__device__ void block_partials(double v[NPAR], double *partial) {
+  __shared__ double sm[NPAR][BLK];
+#pragma unroll
+  for (int i = 0; i < NPAR; ++i) sm[i][threadIdx.x] = v[i];
+  __syncthreads();
+  for (int s = BLK / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int i = 0; i < NPAR; ++i) sm[i][threadIdx.x] += sm[i][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < NPAR) partial[(size_t)blockIdx.x * NPAR + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+// ---------------------------------------------------------------------------
+// collision + streaming adjoint, per fluid node
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(BLK) k_adj_collide(const T *__restrict__ fstate, const float *__restrict__ sb,
+                                                     const uint8_t *__restrict__ mask,
+                                                     const float *__restrict__ lam_next, float *__restrict__ lam_t,
+                                                     Fields d, AdjFields a, double *__restrict__ partial, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  double par[NPAR];
+#pragma unroll
+  for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
+  const size_t N = (size_t)kp.N;
+  if (n < kp.N) {
+    if (mask && mask[n]) {
+#pragma unroll
+      for (int q = 0; q < 27; ++q) lam_t[q * N + n] = 0.0f;
+      for (int c = 0; c < 3; ++c) a.u[c * N + n] = a.F[c * N + n] = a.Q[c * N + n] = 0.0f;
+      a.pm[n] = 0.0f;
+      a.om1[n] = 0.0f;
+      a.rho[n] = 0.0f;
+    } else {
+      a.rho[n] = 0.0f;  // direct density adjoint: none in a step
+      const bool rest = kp.shift_mode == LBM_SHIFT_REST;
+      const float rb = rest ? sb[n] : kp.rho_shift, cb = rest ? sb[N + n] : 0.0f;
+      float f[27];
+#pragma unroll
+      for (int q = 0; q < 27; ++q)
+        f[q] = load_pop<T>(fstate + q * N + n) + (rest ? shift_rest(q, rb, cb) : weight_of(q) * rb);
+      const float ux = d.u[n], uy = d.u[N + n], uz = d.u[2 * N + n];
+      const float Fx = d.F[n], Fy = d.F[N + n], Fz = d.F[2 * N + n];
+      const float Qx = d.Q[n], Qy = d.Q[N + n], Qz = d.Q[2 * N + n];
+      const float r = d.rho[n];
+      const float pm = pm_of(d.mu[n], kp);
+      float om1 = kp.om[1];
+      if (kp.nu > 0.0f) om1 = 1.0f / (r * kp.nu / pm + 0.5f);
+      // forward recompute of the moments
+      float k[27], ks[27];
+      cp27(k, f);
+      to_central(k, ux, uy, uz);
+      cp27(ks, k);
+      collide_cm(ks, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
+      // pull of lambda(t+1): transpose of push with bounce-back
+      Node p = decode(n, kp.nx, kp.ny);
+      float lam[27];
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        if (q == 13) {
+          lam[q] = lam_next[q * N + n];
+          continue;
+        }
+        const int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
+        lam[q] = (mask && mask[m]) ? lam_next[(size_t)(26 - q) * N + n] : lam_next[q * N + m];
+      }
+      float gux = 0.0f, guy = 0.0f, guz = 0.0f;
+      from_central_vjp(lam, ks, ux, uy, uz, gux, guy, guz);
+      float lk[27];
+      float lpm = 0.0f, lFx = 0.0f, lFy = 0.0f, lFz = 0.0f, lQx = 0.0f, lQy = 0.0f, lQz = 0.0f, lom1 = 0.0f;
+      float gom[11];
+#pragma unroll
+      for (int i = 0; i < 11; ++i) gom[i] = 0.0f;
+      collide_vjp(k, lam, lk, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp, lpm, lFx, lFy, lFz, lQx, lQy, lQz, lom1, gom);
+      to_central_vjp(lk, f, ux, uy, uz, gux, guy, guz);
+#pragma unroll
+      for (int q = 0; q < 27; ++q) lam_t[q * N + n] = lk[q];
+      a.u[n] = gux;
+      a.u[N + n] = guy;
+      a.u[2 * N + n] = guz;
+      a.F[n] = lFx;
+      a.F[N + n] = lFy;
+      a.F[2 * N + n] = lFz;
+      a.Q[n] = lQx;
+      a.Q[N + n] = lQy;
+      a.Q[2 * N + n] = lQz;
+      a.pm[n] = lpm;
+      if (kp.nu > 0.0f) {
+        a.om1[n] = lom1;
+      } else {
+        a.om1[n] = 0.0f;
+        gom[1] = lom1;
+      }
+#pragma unroll
+      for (int i = 0; i < 11; ++i) par[1 + i] = gom[i];
+    }
+  }
+  block_partials(par, partial);
+}
+
+// phi_a adjoint: Q_a(x) = -9 sum_q w_q c_qa phi_a(x + c_q)  =>
+// lphi_a(y) = -9 sum_q w_q c_qa lQ_a(y - c_q) (lQ = 0 on solid nodes)
+__global__ void __launch_bounds__(256) k_adj_phi(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N) return;
+  const size_t N = (size_t)kp.N;
+  if (mask && mask[n]) {
+    a.phi[n] = a.phi[N + n] = a.phi[2 * N + n] = 0.0f;
+    return;
+  }
+  Node p = decode(n, kp.nx, kp.ny);
+  float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (q == 13) continue;
+    const int m = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+    if (cx_of(q)) sx += cx_of(q) * weight_of(q) * a.Q[m];
+    if (cy_of(q)) sy += cy_of(q) * weight_of(q) * a.Q[N + m];
+    if (cz_of(q)) sz += cz_of(q) * weight_of(q) * a.Q[2 * N + m];
+  }
+  a.phi[n] = -9.0f * sx;
+  a.phi[N + n] = -9.0f * sy;
+  a.phi[2 * N + n] = -9.0f * sz;
+}
+
+// local field adjoints at a fluid node: writes lrho (local part), lj (into
+// a.Q), lg = adjoint of grad mu (into a.phi), lmu (local part, into a.mu)
+__global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ mask, Fields d, AdjFields a,
+                                                    KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N) return;
+  const size_t N = (size_t)kp.N;
+  if (mask && mask[n]) {
+    a.rho[n] = 0.0f;
+    a.mu[n] = 0.0f;
+    for (int c = 0; c < 3; ++c) a.Q[c * N + n] = a.phi[c * N + n] = 0.0f;
+    return;
+  }
+  const float r = d.rho[n];
+  const float mup = d.mu[n];
+  const float pm = pm_of(mup, kp);
+  const float e = basis_c(r, mup, kp);
+  const float u[3] = {d.u[n], d.u[N + n], d.u[2 * N + n]};
+  const float F[3] = {d.F[n], d.F[N + n], d.F[2 * N + n]};
+  const float c3 = 1.0f / 3.0f - r;
+  float lrho = 0.0f, lpm = a.pm[n];
+  // phi = e u
+  float lu[3], le = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    const float lph = a.phi[c * N + n];
+    le += lph * u[c];
+    lu[c] = a.u[c * N + n] + e * lph;
+  }
+  lpm += le;
+  lrho += -le * (1.0f / 3.0f);
+  // omega_1 = 1 / (rho nu / p_m + 1/2)
+  if (kp.nu > 0.0f) {
+    const float om1 = 1.0f / (r * kp.nu / pm + 0.5f);
+    const float lo = a.om1[n];
+    lrho += lo * (-om1 * om1 * kp.nu / pm);
+    lpm += lo * (om1 * om1 * r * kp.nu / (pm * pm));
+  }
+  // u = (j + F/2)/rho, F = (1/3 - rho) g
+  const float ir = 1.0f / r;
+  float lF[3], lg[3];
+  float udot = 0.0f, Fdotg = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    a.Q[c * N + n] = lu[c] * ir;  // lj
+    lF[c] = a.F[c * N + n] + 0.5f * lu[c] * ir;
+    udot += lu[c] * u[c];
+  }
+  lrho += -udot * ir;
+  for (int c = 0; c < 3; ++c) {
+    const float g = F[c] / c3;  // grad mu recovered from F (rho != 1/3 on fluid nodes)
+    Fdotg += lF[c] * g;
+    lg[c] = c3 * lF[c];
+    a.phi[c * N + n] = lg[c];
+  }
+  lrho += -Fdotg;
+  a.rho[n] += lrho;  // adds to any direct seed
+  a.mu[n] = lpm * (1.0f / 3.0f);
+}
+
+// lmu(y) = local(y) + 3 sum_q w_q sum_a c_qa lg_a(y - c_q)
+__global__ void __launch_bounds__(256) k_adj_mu(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N) return;
+  const size_t N = (size_t)kp.N;
+  Node p = decode(n, kp.nx, kp.ny);
+  float s = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (q == 13) continue;
+    const int m = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+    float v = 0.0f;
+    if (cx_of(q)) v += cx_of(q) * a.phi[m];
+    if (cy_of(q)) v += cy_of(q) * a.phi[N + m];
+    if (cz_of(q)) v += cz_of(q) * a.phi[2 * N + m];
+    s += weight_of(q) * v;
+  }
+  a.pm[n] = ((mask && mask[n]) ? 0.0f : a.mu[n]) + 3.0f * s;  // total lmu into a.pm
+}
+
+// Eq. 36 transposed: mu(b) = sum_q w_q s(b+c_q) mu(b+c_q) / den(b) on solid
+// boundary nodes b.  Gathered at fluid nodes y: sum over solid neighbours
+// b = y - c_q of (w_q / den(b)) lmu(b).
+__device__ __forceinline__ float fluid_weight_sum(const uint8_t *__restrict__ mask, int b, const KParams &kp) {
+  Node p = decode(b, kp.nx, kp.ny);
+  float den = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (q == 13) continue;
+    if (!mask[neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp)]) den += weight_of(q);
+  }
+  return den;
+}
+
+__global__ void __launch_bounds__(256) k_adj_wet_mu(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N || mask[n]) return;
+  Node p = decode(n, kp.nx, kp.ny);
+  float add = 0.0f;
+  for (int q = 0; q < 27; ++q) {
+    if (q == 13) continue;
+    const int b = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+    if (mask[b]) add += weight_of(q) / fluid_weight_sum(mask, b, kp) * a.pm[b];
+  }
+  a.mu[n] = a.pm[n] + add;  // final lmu on fluid nodes into a.mu
+}
+
+// mu(x) = mu0(rho(x)) - kappa 6 (sum_q w_q rho(x+c_q) - rho(x)) on fluid x:
+// lrho(y) += [fluid y] (mu0'(rho) + 6 kappa) lmu(y) - 6 kappa sum_q w_q lmu(y+c_q)
+// and dJ/dkappa += -sum_fluid lmu(x) 6 (sum_q w_q rho(x+c_q) - rho(x)).
+__global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mask, Fields d, AdjFields a,
+                                                 double *__restrict__ partial, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  double par[NPAR];
+#pragma unroll
+  for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
+  if (n < kp.N) {
+    const bool solid = mask && mask[n];
+    const float *lmu = a.mu;  // final lmu on fluid nodes; solid entries are not read
+    Node p = decode(n, kp.nx, kp.ny);
+    float s = 0.0f, lap = 0.0f;
+    const float r = d.rho[n];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      if (q == 13) continue;
+      const int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
+      const bool fm = !(mask && mask[m]);
+      if (fm) s += weight_of(q) * lmu[m];
+      lap += weight_of(q) * (d.rho[m] - r);
+    }
+    float lr;
+    if (solid) {
+      lr = -6.0f * kp.kappa * s;
+    } else {
+      const float l0 = lmu[n];
+      const float om = 1.0f - kp.b * r;
+      const float dmu0 = kp.RT * (1.0f / r + kp.b / om + kp.b / (om * om)) - 2.0f * kp.a;
+      lr = a.rho[n] + dmu0 * l0 - 6.0f * kp.kappa * (s + weight_of(13) * l0 - l0);
+      par[0] = -(double)l0 * 6.0 * (double)lap;
+    }
+    a.phi[n] = lr;  // total lrho into a.phi[0..N)
+  }
+  block_partials(par, partial);
+}
+
+// Eqs. 37-38 transposed, part 1 on the boundary list: the derivative of the
+// solid density with respect to rho_ave (1, phi, or 0 when clamped) and to the
+// wetting value, and the parameter gradient lrho(b) * d rho_s / d value.
+__global__ void __launch_bounds__(BLK) k_adj_wet_prep(const int *__restrict__ bnd, int nb,
+                                                      const uint8_t *__restrict__ mask, Fields d, AdjFields a,
+                                                      double *__restrict__ partial, KParams kp) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double par[NPAR];
+#pragma unroll
+  for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
+  if (t < nb) {
+    const int b = bnd[t];
+    Node p = decode(b, kp.nx, kp.ny);
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      if (q == 13) continue;
+      const int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
+      if (!mask[m]) {
+        num += weight_of(q) * d.rho[m];
+        den += weight_of(q);
+      }
+    }
+    const float ave = num / den;
+    float dave = 1.0f, dval = 0.0f;
+    if (kp.wet_mode != LBM_WET_NEUTRAL && ave >= kp.band_lo && ave <= kp.band_hi) {
+      const float m = kp.wet_mode == LBM_WET_PHI ? kp.wet_value * ave : ave - kp.wet_value;
+      if (m < kp.band_lo || m > kp.band_hi) {
+        dave = 0.0f;
+      } else if (kp.wet_mode == LBM_WET_PHI) {
+        dave = kp.wet_value;
+        dval = ave;
+      } else {
+        dave = 1.0f;
+        dval = -1.0f;
+      }
+    }
+    const float lrs = a.phi[b];
+    par[12] = (double)lrs * dval;
+    a.u[b] = dave / den * lrs;  // scaled adjoint handed to the fluid neighbours
+  }
+  block_partials(par, partial);
+}
+
+// part 2, gathered at fluid nodes: lrho(y) += sum over solid neighbours b of
+// w_q * (dave(b) / den(b)) lrho(b)
+__global__ void __launch_bounds__(256) k_adj_wet_rho(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N || mask[n]) return;
+  Node p = decode(n, kp.nx, kp.ny);
+  float add = 0.0f;
+  for (int q = 0; q < 27; ++q) {
+    if (q == 13) continue;
+    const int b = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+    if (mask[b]) add += weight_of(q) * a.u[b];
+  }
+  a.phi[n] += add;
+}
+
+// lambda_q(t)(x) = local part + lrho(x) + c_q . lj(x) on fluid nodes
+__global__ void __launch_bounds__(256) k_adj_out(const uint8_t *__restrict__ mask, AdjFields a,
+                                                 float *__restrict__ lam_t, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N || (mask && mask[n])) return;
+  const size_t N = (size_t)kp.N;
+  const float lr = a.phi[n], jx = a.Q[n], jy = a.Q[N + n], jz = a.Q[2 * N + n];
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+    lam_t[q * N + n] += lr + cx_of(q) * jx + cy_of(q) * jy + cz_of(q) * jz;
+}
+
+// adds the NPAR block partials of `blocks` blocks into out[0..NPAR) in order
+__global__ void k_adj_reduce(const double *__restrict__ partial, int blocks, double *__restrict__ out) {
+  const int i = threadIdx.x;
+  if (i >= NPAR) return;
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += partial[(size_t)b * NPAR + i];
+  out[i] += s;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the initialisation: f(0) = equilibrium (Eq. 20) about u0 at
+// rho = rho0 and p_m = (1 + mu(rho0))/3
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_init(const uint8_t *__restrict__ mask, const float *__restrict__ u0,
+                                                  const float *__restrict__ lam0, Fields d, AdjFields a, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N) return;
+  const size_t N = (size_t)kp.N;
+  if (mask && mask[n]) {
+    a.rho[n] = 0.0f;
+    a.mu[n] = 0.0f;
+    return;
+  }
+  float lam[27], keq[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    lam[q] = lam0[q * N + n];
+    keq[q] = 0.0f;
+  }
+  const float cs2 = 1.0f / 3.0f, pm = pm_of(d.mu[n], kp);
+  float *k = keq;
+  KM(0, 0, 0) = d.rho[n];
+  KM(2, 0, 0) = KM(0, 2, 0) = KM(0, 0, 2) = pm;
+  KM(2, 2, 0) = KM(2, 0, 2) = KM(0, 2, 2) = pm * cs2;
+  KM(2, 2, 2) = pm * cs2 * cs2;
+  float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+  if (u0) {
+    ux = u0[n];
+    uy = u0[N + n];
+    uz = u0[2 * N + n];
+  }
+  float gx = 0.0f, gy = 0.0f, gz = 0.0f;  // u0 is not differentiated
+  from_central_vjp(lam, keq, ux, uy, uz, gx, gy, gz);
+  float *ls = lam;
+  const float lpm = LS(2, 0, 0) + LS(0, 2, 0) + LS(0, 0, 2) + (LS(2, 2, 0) + LS(2, 0, 2) + LS(0, 2, 2)) * cs2 +
+                    LS(2, 2, 2) * cs2 * cs2;
+  a.rho[n] = LS(0, 0, 0);
+  a.mu[n] = lpm * (1.0f / 3.0f);
+}
+
+// copy lrho (fluid nodes) to the caller's gradient array
+__global__ void __launch_bounds__(256) k_adj_grad_rho0(const uint8_t *__restrict__ mask, AdjFields a,
+                                                       float *__restrict__ g, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < kp.N) g[n] = (mask && mask[n]) ? 0.0f : a.phi[n];
+}
+
+// ---------------------------------------------------------------------------
+// objectives of the current state and their seeds dJ/df
+// ---------------------------------------------------------------------------
+// per-block FP64 partials of the sums an objective needs (into slots 0..2)
+__global__ void __launch_bounds__(BLK) k_obj_sums(int kind, int wall_z, const uint8_t *__restrict__ mask, Fields d,
+                                                  double *__restrict__ partial, KParams kp, float rho_v) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  double par[NPAR];
+#pragma unroll
+  for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
+  if (n < kp.N && !(mask && mask[n])) {
+    const size_t N = (size_t)kp.N;
+    const float r = d.rho[n];
+    Node p = decode(n, kp.nx, kp.ny);
+    if (kind == LBM_OBJ_ENERGY) {
+      const float ux = d.u[n], uy = d.u[N + n], uz = d.u[2 * N + n];
+      par[0] = 0.5 * (double)r * ((double)ux * ux + (double)uy * uy + (double)uz * uz);
+    } else if (kind == LBM_OBJ_CENTROID_X) {
+      par[0] = (double)p.x * (r - rho_v);
+      par[1] = (double)(r - rho_v);
+    } else if (p.z == wall_z + 1) {
+      par[0] = (double)(r - rho_v);
+    }
+  }
+  block_partials(par, partial);
+}
+
+__global__ void k_obj_finish(int kind, const double *__restrict__ partial, int blocks, double *__restrict__ out,
+                             float rho_l, float rho_v) {
+  if (threadIdx.x != 0) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = 0; b < blocks; ++b) {
+    s0 += partial[(size_t)b * NPAR];
+    s1 += partial[(size_t)b * NPAR + 1];
+  }
+  if (kind == LBM_OBJ_ENERGY) {
+    out[0] = s0;
+  } else if (kind == LBM_OBJ_CENTROID_X) {
+    out[0] = s0 / s1;
+    out[1] = s1;
+  } else {
+    const double area = s0 / ((double)rho_l - rho_v);
+    out[0] = sqrt(area / 3.14159265358979323846);
+  }
+}
+
+// seeds of the field adjoints: energy -> lu = rho u, lrho = |u|^2/2 (added
+// after k_adj_fields); centroid -> lrho = (x - J)/W; contact radius ->
+// lrho = 1/(2 pi J (rho_l - rho_v)) on the first fluid layer
+__global__ void __launch_bounds__(256) k_obj_seed(int kind, int wall_z, const uint8_t *__restrict__ mask, Fields d,
+                                                  AdjFields a, const double *__restrict__ Jv, KParams kp,
+                                                  float rho_l, float rho_v) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N) return;
+  const size_t N = (size_t)kp.N;
+  for (int c = 0; c < 3; ++c) a.u[c * N + n] = a.F[c * N + n] = a.phi[c * N + n] = a.Q[c * N + n] = 0.0f;
+  a.pm[n] = 0.0f;
+  a.om1[n] = 0.0f;
+  a.rho[n] = 0.0f;
+  if (mask && mask[n]) return;
+  Node p = decode(n, kp.nx, kp.ny);
+  if (kind == LBM_OBJ_ENERGY) {
+    const float r = d.rho[n];
+    const float ux = d.u[n], uy = d.u[N + n], uz = d.u[2 * N + n];
+    a.u[n] = r * ux;
+    a.u[N + n] = r * uy;
+    a.u[2 * N + n] = r * uz;
+    a.rho[n] = 0.5f * (ux * ux + uy * uy + uz * uz);
+  } else if (kind == LBM_OBJ_CENTROID_X) {
+    a.rho[n] = (float)(((double)p.x - Jv[0]) / Jv[1]);
+  } else if (p.z == wall_z + 1) {
+    a.rho[n] = (float)(1.0 / (2.0 * 3.14159265358979323846 * Jv[0] * ((double)rho_l - rho_v)));
+  }
+}
+
+}  // namespace
+
+void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0) {
+  const KParams &kp = ctx->kp;
+  cudaStream_t s = ctx->stream;
+  const int gb = (kp.N + BLK - 1) / BLK, g = (kp.N + 255) / 256;
+  // fields of the initial density are in ctx->fld (launch_init ran before)
+  k_adj_init<<<g, 256, 0, s>>>(ctx->mask, u0, lam0, ctx->fld, ctx->adj, kp);
+  k_adj_rho<<<gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
+  k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
+  int launches = 3;
+  if (ctx->n_bnd) {
+    const int gw = (ctx->n_bnd + BLK - 1) / BLK;
+    k_adj_wet_prep<<<gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
+    k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gw, grad);
+    k_adj_wet_rho<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+    launches += 3;
+  }
+  k_adj_grad_rho0<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, grad_rho0, kp);
+  ctx->launches += launches + 1;
+}
+
+void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad) {
+  const KParams &kp = ctx->kp;
+  cudaStream_t s = ctx->stream;
+  const int gb = (kp.N + BLK - 1) / BLK, g = (kp.N + 255) / 256;
+  const float rl = (float)ctx->params.rho_l, rv = (float)ctx->params.rho_v;
+  launch_fields_full(ctx);
+  k_obj_sums<<<gb, BLK, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj_partial, kp, rv);
+  k_obj_finish<<<1, 32, 0, s>>>(kind, ctx->adj_partial, gb, J, rl, rv);
+  k_obj_seed<<<g, 256, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj, J, kp, rl, rv);
+  cudaMemsetAsync(lam, 0, 27 * (size_t)kp.N * sizeof(float), s);
+  k_adj_fields<<<g, 256, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
+  k_adj_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+  if (ctx->mask)
+    k_adj_wet_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+  else
+    cudaMemcpyAsync(ctx->adj.mu, ctx->adj.pm, (size_t)kp.N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  // the objective's direct dependence on kappa and on the wetting value
+  k_adj_rho<<<gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
+  if (grad) k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
+  int launches = 9;
+  if (ctx->n_bnd) {
+    const int gw = (ctx->n_bnd + BLK - 1) / BLK;
+    k_adj_wet_prep<<<gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
+    if (grad) k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gw, grad);
+    k_adj_wet_rho<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+    launches += 3;
+  }
+  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, lam, kp);
+  ctx->launches += launches;
+}
+
+void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad) {
+  const KParams &kp = ctx->kp;
+  cudaStream_t s = ctx->stream;
+  // forward recompute of the fields of f(t) (the state is in ctx->f[cur])
+  launch_fields_full(ctx);
+  const int gb = (kp.N + BLK - 1) / BLK, g = (kp.N + 255) / 256;
+  if (ctx->storage == LBM_F16)
+    k_adj_collide<__half><<<gb, BLK, 0, s>>>((const __half *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
+                                            ctx->fld, ctx->adj, ctx->adj_partial, kp);
+  else
+    k_adj_collide<float><<<gb, BLK, 0, s>>>((const float *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
+                                           ctx->fld, ctx->adj, ctx->adj_partial, kp);
+  k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
+  k_adj_phi<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+  k_adj_fields<<<g, 256, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
+  k_adj_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+  if (ctx->mask) {
+    k_adj_wet_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+  } else {
+    cudaMemcpyAsync(ctx->adj.mu, ctx->adj.pm, (size_t)kp.N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  }
+  k_adj_rho<<<gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
+  k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
+  if (ctx->n_bnd) {
+    const int gw = (ctx->n_bnd + BLK - 1) / BLK;
+    k_adj_wet_prep<<<gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
+    k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gw, grad);
+    k_adj_wet_rho<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+  }
+  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, lam_t, kp);
+  ctx->launches += 9 + (ctx->n_bnd ? 3 : 0);
+}
+
+}  // namespace lbm

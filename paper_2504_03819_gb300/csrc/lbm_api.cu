@@ -23,8 +23,9 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 //   boundary list   N ints
 //   reduction       RED_BLOCKS * 2 doubles
 //   status          2 ints
+//   adjoint         16 N floats, then ceil(N/128) * LBM_NGRAD doubles
 struct Layout {
-  size_t f0, f1, fields, bnd, red, status, total;
+  size_t f0, f1, fields, bnd, red, status, adj, adj_partial, total;
 };
 
 bool layout(int nx, int ny, int nz, int storage, Layout *L) {
@@ -40,6 +41,8 @@ bool layout(int nx, int ny, int nz, int storage, Layout *L) {
   L->bnd = off; off = align_up(off + (size_t)N * sizeof(int));
   L->red = off; off = align_up(off + (size_t)RED_BLOCKS * 2 * sizeof(double));
   L->status = off; off = align_up(off + 2 * sizeof(int));
+  L->adj = off; off = align_up(off + 16 * (size_t)N * sizeof(float));
+  L->adj_partial = off; off = align_up(off + (size_t)((N + 127) / 128 + 1) * LBM_NGRAD * sizeof(double));
   L->total = off;
   return true;
 }
@@ -150,6 +153,16 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
   ctx->bnd = (int *)(base + L.bnd);
   ctx->red_partial = (double *)(base + L.red);
   ctx->status = (int *)(base + L.status);
+  float *ad = (float *)(base + L.adj);
+  ctx->adj.u = ad;
+  ctx->adj.F = ad + 3 * N;
+  ctx->adj.Q = ad + 6 * N;
+  ctx->adj.phi = ad + 9 * N;
+  ctx->adj.pm = ad + 12 * N;
+  ctx->adj.om1 = ad + 13 * N;
+  ctx->adj.rho = ad + 14 * N;
+  ctx->adj.mu = ad + 15 * N;
+  ctx->adj_partial = (double *)(base + L.adj_partial);
   ctx->kp.nx = nx;
   ctx->kp.ny = ny;
   ctx->kp.nz = nz;
@@ -320,6 +333,37 @@ int lbm_set_populations(lbm_ctx *ctx, const float *f) {
   int rc = check_cuda(ctx, "lbm_set_populations");
   if (rc == LBM_OK) ctx->have_state = 1;
   return rc;
+}
+
+int lbm_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad_params) {
+  if (!ctx || !J || !lam) return LBM_ERR_ARG;
+  if (!ctx->have_state) return fail(ctx, LBM_ERR_STATE, "no state");
+  if (kind < LBM_OBJ_ENERGY || kind > LBM_OBJ_CONTACT_RADIUS) return fail(ctx, LBM_ERR_ARG, "unknown objective");
+  if (kind == LBM_OBJ_CONTACT_RADIUS && (wall_z < 0 || wall_z + 1 >= ctx->nz))
+    return fail(ctx, LBM_ERR_ARG, "wall_z + 1 must be a plane of the domain");
+  if (kind != LBM_OBJ_ENERGY && !(ctx->params.rho_l > ctx->params.rho_v))
+    return fail(ctx, LBM_ERR_ARG, "objective needs rho_l > rho_v in the parameters");
+  cudaGetLastError();
+  launch_objective(ctx, kind, wall_z, J, lam, grad_params);
+  return check_cuda(ctx, "lbm_objective");
+}
+
+int lbm_adjoint_step(lbm_ctx *ctx, const void *state_t, const float *lam_next, float *lam_t, double *grad_params) {
+  if (!ctx || !state_t || !lam_next || !lam_t || !grad_params || (const void *)lam_next == (const void *)lam_t)
+    return LBM_ERR_ARG;
+  int rc = lbm_set_raw_state(ctx, state_t);
+  if (rc != LBM_OK) return rc;
+  launch_adjoint_step(ctx, ctx->f[ctx->cur], lam_next, lam_t, grad_params);
+  return check_cuda(ctx, "lbm_adjoint_step");
+}
+
+int lbm_adjoint_init(lbm_ctx *ctx, const float *rho0, const float *u0, const float *lam0, double *grad_params,
+                     float *grad_rho0) {
+  if (!ctx || !rho0 || !lam0 || !grad_params || !grad_rho0) return LBM_ERR_ARG;
+  int rc = lbm_set_state(ctx, rho0, u0);  // fields of rho0 in the workspace
+  if (rc != LBM_OK) return rc;
+  launch_adjoint_init(ctx, u0, lam0, grad_params, grad_rho0);
+  return check_cuda(ctx, "lbm_adjoint_init");
 }
 
 const char *lbm_last_error(const lbm_ctx *ctx) {

@@ -461,6 +461,12 @@ void launch_step_staged(lbm_ctx *ctx) {
     step_impl<float>(ctx);
 }
 
+void launch_fields_full(lbm_ctx *ctx) {
+  launch_fields(ctx, true);
+  k_q<<<blocks_for(ctx->N), BLOCK, 0, ctx->stream>>>(ctx->fld.phi, ctx->mask, ctx->fld.Q, ctx->kp);
+  ctx->launches++;
+}
+
 void launch_wet_rho(lbm_ctx *ctx) {
   TimedLaunch t(ctx, K_WET_RHO);
   k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld.rho, ctx->kp);

@@ -43,6 +43,12 @@ struct Fields {
   float *sb;   // 2N    shift bases of LBM_SHIFT_REST: rho, then p_m - rho/3
 };
 
+// Adjoint scratch (reused between the stages of one adjoint step).
+struct AdjFields {
+  float *u, *F, *Q, *phi;  // 3N each
+  float *pm, *om1, *rho, *mu;  // N each
+};
+
 enum KernelId {
   K_MOMENTS = 0,
   K_WET_RHO,
@@ -71,6 +77,8 @@ struct lbm_ctx {
   int cur;
   lbm::Fields fld;
   double *red_partial;  // RED_BLOCKS * 2
+  lbm::AdjFields adj;   // adjoint scratch
+  double *adj_partial;  // per-block FP64 parameter-gradient partials
   int *status;          // [0] status bits, [1] counter scratch
   lbm_params params;
   lbm::KParams kp;
@@ -104,6 +112,10 @@ void launch_init(lbm_ctx *ctx, const float *rho0, const float *u0);
 void launch_reduce(lbm_ctx *ctx, double *out);
 void launch_get_populations(lbm_ctx *ctx, float *out);
 void launch_copy_mu(lbm_ctx *ctx, float *out);       // mu' + mu_ref
+void launch_fields_full(lbm_ctx *ctx);               // rho, j, mu', u, F, phi, Q of the current state
+void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad);
+void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0);
+void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad);
 void launch_set_populations(lbm_ctx *ctx, const float *in);
 const char *kernel_name(int id);
 
