@@ -245,6 +245,20 @@ int lbm_adjoint_step(lbm_ctx *ctx, const void *state_t, const float *lam_next, f
 int lbm_adjoint_init(lbm_ctx *ctx, const float *rho0, const float *u0, const float *lam0,
                      double *grad_params, float *grad_rho0);
 
+/*
+ * Adjoint sweep over one checkpoint segment of n >= 1 steps, enqueued from
+ * the library (no per-step host round trip).  ckpt: raw state at t0
+ * (device, lbm_state_bytes bytes); state_pool: device buffer of
+ * n * lbm_state_bytes bytes that receives the recomputed states t0 ..
+ * t0+n-1 (the step writes into it directly); lam: device, 27*N floats, on
+ * entry dJ/df(t0+n), on return dJ/df(t0); lam_tmp: device, 27*N floats of
+ * scratch; grad_params: accumulated as in lbm_adjoint_step.  The context's
+ * current state becomes ckpt.  Equivalent to n calls of lbm_adjoint_step on
+ * the recomputed states.
+ */
+int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool, float *lam, float *lam_tmp,
+                        double *grad_params);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Number of kernels this context has launched since init. */

@@ -32,26 +32,27 @@ def theta_of(p: Params) -> torch.Tensor:
 def forward_checkpoints(dom: Domain, rho0, u0, nsteps: int, K: int) -> dict:
     dom.set_state(rho0, u0)
     ckpts = {0: dom.get_state().clone()}
-    for s in range(1, nsteps + 1):
-        dom.step(1)
-        if s % K == 0 and s < nsteps:
-            ckpts[s] = dom.get_state().clone()
+    s = 0
+    while s < nsteps:
+        k = min(K, nsteps - s)
+        dom.step(k)
+        s += k
+        if s < nsteps:
+            ckpts[s] = dom.get_state(sync=False).clone()
     return ckpts
 
 
 def backward_from(dom: Domain, ckpts: dict, nsteps: int, lam, grad, rho0, u0):
-    """Adjoint sweep from dJ/df(T) = lam back to dJ/drho0."""
+    """Adjoint sweep from dJ/df(T) = lam back to dJ/drho0: one
+    lbm_adjoint_segment per checkpoint segment, last to first."""
+    seg = max(b - a for a, b in zip(sorted(ckpts), sorted(ckpts)[1:] + [nsteps]))
+    pool = torch.empty(seg * dom.state_bytes(), dtype=torch.uint8, device=dom.device)
+    lam_a, lam_b = lam.clone(), torch.empty_like(lam)
     t_end = nsteps
     for s0 in sorted(ckpts, reverse=True):
-        dom.set_raw_state(ckpts[s0])
-        states = [ckpts[s0]]
-        for _ in range(s0 + 1, t_end):
-            dom.step(1)
-            states.append(dom.get_state().clone())
-        for k in range(t_end - 1, s0 - 1, -1):
-            lam = dom.adjoint_step(states[k - s0], lam, grad)
+        dom.adjoint_segment(ckpts[s0], t_end - s0, pool, lam_a, lam_b, grad)
         t_end = s0
-    return dom.adjoint_init(rho0, u0, lam, grad)
+    return dom.adjoint_init(rho0, u0, lam_a, grad)
 
 
 def rollout_gradient(dom: Domain, rho0, u0, nsteps: int, K: int, objective: int, wall_z: int = 0):

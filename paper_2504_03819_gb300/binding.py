@@ -41,6 +41,8 @@ SIGNATURES = {
     "lbm_set_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_objective": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_adjoint_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_adjoint_segment": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "lbm_adjoint_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_destroy": (None, [C.c_void_p]),
@@ -245,19 +247,22 @@ class Domain:
     def state_bytes(self) -> int:
         return int(self.lib.lbm_state_bytes(self.ctx))
 
-    def get_state(self):
+    def get_state(self, out=None, sync: bool = True):
         """Raw state as a flat uint8 device tensor (lbm_state_bytes bytes)."""
         t = self.torch
-        out = t.empty(self.state_bytes(), dtype=t.uint8, device=self.device)
+        if out is None:
+            out = t.empty(self.state_bytes(), dtype=t.uint8, device=self.device)
         self._check(self.lib.lbm_get_state(self.ctx, _ptr(out)), "lbm_get_state")
-        self.stream.synchronize()
+        if sync:
+            self.stream.synchronize()
         return out
 
-    def set_raw_state(self, raw):
+    def set_raw_state(self, raw, sync: bool = True):
         raw = raw.to(device=self.device, dtype=self.torch.uint8).contiguous()
         assert raw.numel() == self.state_bytes()
         self._check(self.lib.lbm_set_raw_state(self.ctx, _ptr(raw)), "lbm_set_raw_state")
-        self.stream.synchronize()
+        if sync:
+            self.stream.synchronize()
 
     def get_populations(self):
         t = self.torch
@@ -293,6 +298,14 @@ class Domain:
         self._check(self.lib.lbm_adjoint_step(self.ctx, _ptr(raw), _ptr(lam_next), _ptr(out), _ptr(grad)),
                     "lbm_adjoint_step")
         return out
+
+    def adjoint_segment(self, ckpt, n: int, pool, lam, lam_tmp, grad):
+        """In place: lam = dJ/df(t0+n) -> dJ/df(t0) over the n steps after the
+        raw checkpoint ckpt; pool holds >= n raw states (uint8, CUDA)."""
+        assert pool.numel() >= n * self.state_bytes() and grad.numel() == NGRAD
+        self._check(self.lib.lbm_adjoint_segment(self.ctx, _ptr(ckpt), int(n), _ptr(pool), _ptr(lam),
+                                                 _ptr(lam_tmp), _ptr(grad)), "lbm_adjoint_segment")
+        return lam
 
     def adjoint_init(self, rho0, u0, lam0, grad):
         """dJ/drho0 from dJ/df(0); adds the initialisation's parameter

@@ -12,16 +12,16 @@
 //                       collision (Eqs. 21-26, 28) and of the forward CM
 //                       transform (Eq. 19), with the u-derivatives of both
 //                       transforms; adjoint sources for u, F, Q, p_m, omega_1
-//   k_adj_phi           Q_aa = -3 d_a phi_a (Eq. 27) transposed
-//   k_adj_fields        phi = (p_m - rho/3) u, u = (j + F/2)/rho,
+//   k_adj_fields        Q_aa = -3 d_a phi_a (Eq. 27) transposed (a gather),
+//                       phi = (p_m - rho/3) u, u = (j + F/2)/rho,
 //                       F = (1/3 - rho) grad mu (Eq. 12), p_m = (1 + mu)/3,
 //                       per-node omega_1 (Sec. II B) transposed
 //   k_adj_mu            grad mu transposed (a gather) + the local p_m term
 //   k_adj_wet_mu        Eq. 36 transposed (solid -> fluid neighbours)
 //   k_adj_rho           mu = mu0(rho) - kappa lap rho (Eqs. 2, 32) transposed
 //   k_adj_wet_prep /    Eqs. 37-38 transposed (branch of the forward pass:
-//   k_adj_wet_rho       clamped densities pass no gradient)
-//   k_adj_out           lambda_q(t) = local part + lambda_rho + c_q . lambda_j
+//   k_adj_out           clamped densities pass no gradient), then
+//                       lambda_q(t) = local part + lambda_rho + c_q . lambda_j
 //
 // Parameter gradients are summed per block in FP64 and reduced in a fixed
 // order (deterministic).
@@ -76,35 +76,37 @@ __device__ __forceinline__ void cp27(float *d, const float *s) {
 // x-pass: (q, q+1, q+2), q = 0, 3, ..., 24.
 
 // lam <- (d from_central / d k)^T lam, accumulating d/du into gu.  kin are the
-// post-collision moments (input of from_central).
+// post-collision moments (input of from_central).  The intermediate stages of
+// from_central are recomputed from kin one at a time (one scratch array).
 __device__ __forceinline__ void from_central_vjp(float lam[27], const float kin[27], float ux, float uy, float uz,
                                                  float &gux, float &guy, float &guz) {
-  // stage values: K0 = kin, K1 = after x-pass, K2 = after y-pass
-  float K1[27], K2[27];
-  cp27(K1, kin);
+  float K[27];
+  // z-pass (last) transposed; its inputs are Y(X(kin))
+  cp27(K, kin);
 #pragma unroll
-  for (int q = 0; q < 27; q += 3) cm_axis_inv(K1[q], K1[q + 1], K1[q + 2], ux);
-  cp27(K2, K1);
+  for (int q = 0; q < 27; q += 3) cm_axis_inv(K[q], K[q + 1], K[q + 2], ux);
 #pragma unroll
   for (int g = 0; g < 3; ++g)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) cm_axis_inv(K2[a + 9 * g], K2[a + 3 + 9 * g], K2[a + 6 + 9 * g], uy);
-  // z-pass (last) transposed, inputs K2
+    for (int a = 0; a < 3; ++a) cm_axis_inv(K[a + 9 * g], K[a + 3 + 9 * g], K[a + 6 + 9 * g], uy);
 #pragma unroll
   for (int p = 0; p < 9; ++p) {
-    guz += inv_du(K2[p], K2[p + 9], lam[p], lam[p + 9], lam[p + 18], uz);
+    guz += inv_du(K[p], K[p + 9], lam[p], lam[p + 9], lam[p + 18], uz);
     inv_T(lam[p], lam[p + 9], lam[p + 18], uz);
   }
-  // y-pass transposed, inputs K1
+  // y-pass transposed; its inputs are X(kin)
+  cp27(K, kin);
+#pragma unroll
+  for (int q = 0; q < 27; q += 3) cm_axis_inv(K[q], K[q + 1], K[q + 2], ux);
 #pragma unroll
   for (int g = 0; g < 3; ++g)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int i0 = a + 9 * g, i1 = a + 3 + 9 * g, i2 = a + 6 + 9 * g;
-      guy += inv_du(K1[i0], K1[i1], lam[i0], lam[i1], lam[i2], uy);
+      guy += inv_du(K[i0], K[i1], lam[i0], lam[i1], lam[i2], uy);
       inv_T(lam[i0], lam[i1], lam[i2], uy);
     }
-  // x-pass transposed, inputs K0 = kin
+  // x-pass transposed; its inputs are kin
 #pragma unroll
   for (int q = 0; q < 27; q += 3) {
     gux += inv_du(kin[q], kin[q + 1], lam[q], lam[q + 1], lam[q + 2], ux);
@@ -113,35 +115,36 @@ __device__ __forceinline__ void from_central_vjp(float lam[27], const float kin[
 }
 
 // lam <- (d to_central / d f)^T lam, accumulating d/du.  f are the populations
-// (input of to_central).
+// (input of to_central); stages are recomputed from f one at a time.
 __device__ __forceinline__ void to_central_vjp(float lam[27], const float f[27], float ux, float uy, float uz,
                                                float &gux, float &guy, float &guz) {
-  // stage values: G0 = f, G1 = after z-pass, G2 = after y-pass
-  float G1[27], G2[27];
-  cp27(G1, f);
+  float G[27];
+  // x-pass (last) transposed; its inputs are Y(Z(f))
+  cp27(G, f);
 #pragma unroll
-  for (int p = 0; p < 9; ++p) cm_axis(G1[p], G1[p + 9], G1[p + 18], uz);
-  cp27(G2, G1);
+  for (int p = 0; p < 9; ++p) cm_axis(G[p], G[p + 9], G[p + 18], uz);
 #pragma unroll
   for (int g = 0; g < 3; ++g)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) cm_axis(G2[a + 9 * g], G2[a + 3 + 9 * g], G2[a + 6 + 9 * g], uy);
-  // x-pass (last) transposed, inputs G2
+    for (int a = 0; a < 3; ++a) cm_axis(G[a + 9 * g], G[a + 3 + 9 * g], G[a + 6 + 9 * g], uy);
 #pragma unroll
   for (int q = 0; q < 27; q += 3) {
-    gux += fwd_du(G2[q], G2[q + 1], G2[q + 2], ux, lam[q + 1], lam[q + 2]);
+    gux += fwd_du(G[q], G[q + 1], G[q + 2], ux, lam[q + 1], lam[q + 2]);
     fwd_T(lam[q], lam[q + 1], lam[q + 2], ux);
   }
-  // y-pass transposed, inputs G1
+  // y-pass transposed; its inputs are Z(f)
+  cp27(G, f);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) cm_axis(G[p], G[p + 9], G[p + 18], uz);
 #pragma unroll
   for (int g = 0; g < 3; ++g)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int i0 = a + 9 * g, i1 = a + 3 + 9 * g, i2 = a + 6 + 9 * g;
-      guy += fwd_du(G1[i0], G1[i1], G1[i2], uy, lam[i1], lam[i2]);
+      guy += fwd_du(G[i0], G[i1], G[i2], uy, lam[i1], lam[i2]);
       fwd_T(lam[i0], lam[i1], lam[i2], uy);
     }
-  // z-pass transposed, inputs f
+  // z-pass transposed; its inputs are f
 #pragma unroll
   for (int p = 0; p < 9; ++p) {
     guz += fwd_du(f[p], f[p + 9], f[p + 18], uz, lam[p + 9], lam[p + 18]);
@@ -297,7 +300,7 @@ __device__ void block_partials(double v[NPAR], double *partial) {
 // collision + streaming adjoint, per fluid node
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(BLK) k_adj_collide(const T *__restrict__ fstate, const float *__restrict__ sb,
+__global__ void __launch_bounds__(BLK, 3) k_adj_collide(const T *__restrict__ fstate, const float *__restrict__ sb,
                                                      const uint8_t *__restrict__ mask,
                                                      const float *__restrict__ lam_next, float *__restrict__ lam_t,
                                                      Fields d, AdjFields a, double *__restrict__ partial, KParams kp) {
@@ -318,10 +321,11 @@ __global__ void __launch_bounds__(BLK) k_adj_collide(const T *__restrict__ fstat
       a.rho[n] = 0.0f;  // direct density adjoint: none in a step
       const bool rest = kp.shift_mode == LBM_SHIFT_REST;
       const float rb = rest ? sb[n] : kp.rho_shift, cb = rest ? sb[N + n] : 0.0f;
-      float f[27];
+      auto load_f = [&](float f[27]) {
 #pragma unroll
-      for (int q = 0; q < 27; ++q)
-        f[q] = load_pop<T>(fstate + q * N + n) + (rest ? shift_rest(q, rb, cb) : weight_of(q) * rb);
+        for (int q = 0; q < 27; ++q)
+          f[q] = load_pop<T>(fstate + q * N + n) + (rest ? shift_rest(q, rb, cb) : weight_of(q) * rb);
+      };
       const float ux = d.u[n], uy = d.u[N + n], uz = d.u[2 * N + n];
       const float Fx = d.F[n], Fy = d.F[N + n], Fz = d.F[2 * N + n];
       const float Qx = d.Q[n], Qy = d.Q[N + n], Qz = d.Q[2 * N + n];
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(BLK) k_adj_collide(const T *__restrict__ fstat
       if (kp.nu > 0.0f) om1 = 1.0f / (r * kp.nu / pm + 0.5f);
       // forward recompute of the moments
       float k[27], ks[27];
-      cp27(k, f);
+      load_f(k);
       to_central(k, ux, uy, uz);
       cp27(ks, k);
       collide_cm(ks, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
@@ -355,6 +359,8 @@ __global__ void __launch_bounds__(BLK) k_adj_collide(const T *__restrict__ fstat
 #pragma unroll
       for (int i = 0; i < 11; ++i) gom[i] = 0.0f;
       collide_vjp(k, lam, lk, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp, lpm, lFx, lFy, lFz, lQx, lQy, lQz, lom1, gom);
+      float f[27];  // populations reloaded (L2) rather than kept live
+      load_f(f);
       to_central_vjp(lk, f, ux, uy, uz, gux, guy, guz);
 #pragma unroll
       for (int q = 0; q < 27; ++q) lam_t[q * N + n] = lk[q];
@@ -381,33 +387,12 @@ __global__ void __launch_bounds__(BLK) k_adj_collide(const T *__restrict__ fstat
   block_partials(par, partial);
 }
 
-// phi_a adjoint: Q_a(x) = -9 sum_q w_q c_qa phi_a(x + c_q)  =>
-// lphi_a(y) = -9 sum_q w_q c_qa lQ_a(y - c_q) (lQ = 0 on solid nodes)
-__global__ void __launch_bounds__(256) k_adj_phi(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N) return;
-  const size_t N = (size_t)kp.N;
-  if (mask && mask[n]) {
-    a.phi[n] = a.phi[N + n] = a.phi[2 * N + n] = 0.0f;
-    return;
-  }
-  Node p = decode(n, kp.nx, kp.ny);
-  float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    if (q == 13) continue;
-    const int m = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
-    if (cx_of(q)) sx += cx_of(q) * weight_of(q) * a.Q[m];
-    if (cy_of(q)) sy += cy_of(q) * weight_of(q) * a.Q[N + m];
-    if (cz_of(q)) sz += cz_of(q) * weight_of(q) * a.Q[2 * N + m];
-  }
-  a.phi[n] = -9.0f * sx;
-  a.phi[N + n] = -9.0f * sy;
-  a.phi[2 * N + n] = -9.0f * sz;
-}
-
-// local field adjoints at a fluid node: writes lrho (local part), lj (into
-// a.Q), lg = adjoint of grad mu (into a.phi), lmu (local part, into a.mu)
+// local field adjoints at a fluid node.  First lphi(x) by the transposed
+// Q stencil, lphi_a(x) = -9 sum_q w_q c_qa lQ_a(x - c_q) (a gather of a.Q,
+// zero on solid nodes); then phi = (p_m - rho/3) u, omega_1(rho, p_m),
+// u = (j + F/2)/rho, F = (1/3 - rho) g and p_m = (1 + mu)/3 transposed.
+// Writes lrho (added to a.rho), lj (into a.u), lg = adjoint of grad mu (into
+// a.phi) and the local lmu (into a.mu).
 __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ mask, Fields d, AdjFields a,
                                                     KParams kp) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -416,8 +401,18 @@ __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ 
   if (mask && mask[n]) {
     a.rho[n] = 0.0f;
     a.mu[n] = 0.0f;
-    for (int c = 0; c < 3; ++c) a.Q[c * N + n] = a.phi[c * N + n] = 0.0f;
+    for (int c = 0; c < 3; ++c) a.u[c * N + n] = a.phi[c * N + n] = 0.0f;
     return;
+  }
+  Node p = decode(n, kp.nx, kp.ny);
+  float lph[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (q == 13) continue;
+    const int m = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+    if (cx_of(q)) lph[0] += cx_of(q) * weight_of(q) * a.Q[m];
+    if (cy_of(q)) lph[1] += cy_of(q) * weight_of(q) * a.Q[N + m];
+    if (cz_of(q)) lph[2] += cz_of(q) * weight_of(q) * a.Q[2 * N + m];
   }
   const float r = d.rho[n];
   const float mup = d.mu[n];
@@ -430,9 +425,9 @@ __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ 
   // phi = e u
   float lu[3], le = 0.0f;
   for (int c = 0; c < 3; ++c) {
-    const float lph = a.phi[c * N + n];
-    le += lph * u[c];
-    lu[c] = a.u[c * N + n] + e * lph;
+    lph[c] *= -9.0f;
+    le += lph[c] * u[c];
+    lu[c] = a.u[c * N + n] + e * lph[c];
   }
   lpm += le;
   lrho += -le * (1.0f / 3.0f);
@@ -445,21 +440,16 @@ __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ 
   }
   // u = (j + F/2)/rho, F = (1/3 - rho) g
   const float ir = 1.0f / r;
-  float lF[3], lg[3];
   float udot = 0.0f, Fdotg = 0.0f;
   for (int c = 0; c < 3; ++c) {
-    a.Q[c * N + n] = lu[c] * ir;  // lj
-    lF[c] = a.F[c * N + n] + 0.5f * lu[c] * ir;
+    const float lF = a.F[c * N + n] + 0.5f * lu[c] * ir;
     udot += lu[c] * u[c];
-  }
-  lrho += -udot * ir;
-  for (int c = 0; c < 3; ++c) {
     const float g = F[c] / c3;  // grad mu recovered from F (rho != 1/3 on fluid nodes)
-    Fdotg += lF[c] * g;
-    lg[c] = c3 * lF[c];
-    a.phi[c * N + n] = lg[c];
+    Fdotg += lF * g;
+    a.phi[c * N + n] = c3 * lF;   // lg
+    a.u[c * N + n] = lu[c] * ir;  // lj
   }
-  lrho += -Fdotg;
+  lrho += -udot * ir - Fdotg;
   a.rho[n] += lrho;  // adds to any direct seed
   a.mu[n] = lpm * (1.0f / 3.0f);
 }
@@ -515,14 +505,14 @@ __global__ void __launch_bounds__(256) k_adj_wet_mu(const uint8_t *__restrict__ 
 // lrho(y) += [fluid y] (mu0'(rho) + 6 kappa) lmu(y) - 6 kappa sum_q w_q lmu(y+c_q)
 // and dJ/dkappa += -sum_fluid lmu(x) 6 (sum_q w_q rho(x+c_q) - rho(x)).
 __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mask, Fields d, AdjFields a,
-                                                 double *__restrict__ partial, KParams kp) {
+                                                 const float *__restrict__ lmu, double *__restrict__ partial,
+                                                 KParams kp) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   double par[NPAR];
 #pragma unroll
   for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
   if (n < kp.N) {
-    const bool solid = mask && mask[n];
-    const float *lmu = a.mu;  // final lmu on fluid nodes; solid entries are not read
+    const bool solid = mask && mask[n];  // lmu: final lmu on fluid nodes; solid entries are not read
     Node p = decode(n, kp.nx, kp.ny);
     float s = 0.0f, lap = 0.0f;
     const float r = d.rho[n];
@@ -588,45 +578,51 @@ __global__ void __launch_bounds__(BLK) k_adj_wet_prep(const int *__restrict__ bn
     }
     const float lrs = a.phi[b];
     par[12] = (double)lrs * dval;
-    a.u[b] = dave / den * lrs;  // scaled adjoint handed to the fluid neighbours
+    a.F[b] = dave / den * lrs;  // scaled adjoint handed to the fluid neighbours
   }
   block_partials(par, partial);
 }
 
-// part 2, gathered at fluid nodes: lrho(y) += sum over solid neighbours b of
-// w_q * (dave(b) / den(b)) lrho(b)
-__global__ void __launch_bounds__(256) k_adj_wet_rho(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N || mask[n]) return;
-  Node p = decode(n, kp.nx, kp.ny);
-  float add = 0.0f;
-  for (int q = 0; q < 27; ++q) {
-    if (q == 13) continue;
-    const int b = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
-    if (mask[b]) add += weight_of(q) * a.u[b];
-  }
-  a.phi[n] += add;
-}
-
-// lambda_q(t)(x) = local part + lrho(x) + c_q . lj(x) on fluid nodes
-__global__ void __launch_bounds__(256) k_adj_out(const uint8_t *__restrict__ mask, AdjFields a,
+// lambda_q(t)(x) = local part + lrho(x) + c_q . lj(x) on fluid nodes, with
+// part 2 of Eqs. 37-38 transposed when there are walls: lrho(y) += sum over
+// solid neighbours b of w_q (dave(b)/den(b)) lrho(b) (stored in a.F).
+__global__ void __launch_bounds__(256) k_adj_out(const uint8_t *__restrict__ mask, int wet, AdjFields a,
                                                  float *__restrict__ lam_t, KParams kp) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= kp.N || (mask && mask[n])) return;
   const size_t N = (size_t)kp.N;
-  const float lr = a.phi[n], jx = a.Q[n], jy = a.Q[N + n], jz = a.Q[2 * N + n];
+  float lr = a.phi[n];
+  if (wet) {
+    Node p = decode(n, kp.nx, kp.ny);
+    for (int q = 0; q < 27; ++q) {
+      if (q == 13) continue;
+      const int b = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+      if (mask[b]) lr += weight_of(q) * a.F[b];
+    }
+  }
+  const float jx = a.u[n], jy = a.u[N + n], jz = a.u[2 * N + n];
 #pragma unroll
   for (int q = 0; q < 27; ++q)
     lam_t[q * N + n] += lr + cx_of(q) * jx + cy_of(q) * jy + cz_of(q) * jz;
 }
 
-// adds the NPAR block partials of `blocks` blocks into out[0..NPAR) in order
-__global__ void k_adj_reduce(const double *__restrict__ partial, int blocks, double *__restrict__ out) {
-  const int i = threadIdx.x;
-  if (i >= NPAR) return;
+// adds the NPAR block partials of `blocks` blocks into out[0..NPAR): one
+// block per parameter, each thread a fixed strided subset, then a fixed tree
+// (deterministic)
+constexpr int RB = 256;
+__global__ void __launch_bounds__(RB) k_adj_reduce(const double *__restrict__ partial, int blocks,
+                                                   double *__restrict__ out) {
+  __shared__ double sm[RB];
+  const int i = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < blocks; ++b) s += partial[(size_t)b * NPAR + i];
-  out[i] += s;
+  for (int b = threadIdx.x; b < blocks; b += RB) s += partial[(size_t)b * NPAR + i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = RB / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] += sm[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -670,11 +666,26 @@ __global__ void __launch_bounds__(256) k_adj_init(const uint8_t *__restrict__ ma
   a.mu[n] = lpm * (1.0f / 3.0f);
 }
 
-// copy lrho (fluid nodes) to the caller's gradient array
-__global__ void __launch_bounds__(256) k_adj_grad_rho0(const uint8_t *__restrict__ mask, AdjFields a,
+// lrho (fluid nodes, with the wetting part gathered from solid neighbours)
+// into the caller's gradient array
+__global__ void __launch_bounds__(256) k_adj_grad_rho0(const uint8_t *__restrict__ mask, int wet, AdjFields a,
                                                        float *__restrict__ g, KParams kp) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < kp.N) g[n] = (mask && mask[n]) ? 0.0f : a.phi[n];
+  if (n >= kp.N) return;
+  if (mask && mask[n]) {
+    g[n] = 0.0f;
+    return;
+  }
+  float lr = a.phi[n];
+  if (wet) {
+    Node p = decode(n, kp.nx, kp.ny);
+    for (int q = 0; q < 27; ++q) {
+      if (q == 13) continue;
+      const int b = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+      if (mask[b]) lr += weight_of(q) * a.F[b];
+    }
+  }
+  g[n] = lr;
 }
 
 // ---------------------------------------------------------------------------
@@ -704,14 +715,26 @@ __global__ void __launch_bounds__(BLK) k_obj_sums(int kind, int wall_z, const ui
   block_partials(par, partial);
 }
 
-__global__ void k_obj_finish(int kind, const double *__restrict__ partial, int blocks, double *__restrict__ out,
-                             float rho_l, float rho_v) {
-  if (threadIdx.x != 0) return;
-  double s0 = 0.0, s1 = 0.0;
-  for (int b = 0; b < blocks; ++b) {
-    s0 += partial[(size_t)b * NPAR];
-    s1 += partial[(size_t)b * NPAR + 1];
+__global__ void __launch_bounds__(RB) k_obj_finish(int kind, const double *__restrict__ partial, int blocks,
+                                                   double *__restrict__ out, float rho_l, float rho_v) {
+  __shared__ double sm[2][RB];
+  double a0 = 0.0, a1 = 0.0;
+  for (int b = threadIdx.x; b < blocks; b += RB) {
+    a0 += partial[(size_t)b * NPAR];
+    a1 += partial[(size_t)b * NPAR + 1];
   }
+  sm[0][threadIdx.x] = a0;
+  sm[1][threadIdx.x] = a1;
+  __syncthreads();
+  for (int w = RB / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + w];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double s0 = sm[0][0], s1 = sm[1][0];
   if (kind == LBM_OBJ_ENERGY) {
     out[0] = s0;
   } else if (kind == LBM_OBJ_CENTROID_X) {
@@ -754,88 +777,110 @@ __global__ void __launch_bounds__(256) k_obj_seed(int kind, int wall_z, const ui
 
 }  // namespace
 
+// Parameter partials: region 0 (collision), region 1 (mu -> rho), region 2
+// (wetting) lie back to back in ctx->adj_partial and are summed by one
+// k_adj_reduce over all their blocks.
+struct Regions {
+  double *collide, *rho, *wet;
+  int gb, gw;
+};
+
+Regions regions(lbm_ctx *ctx) {
+  Regions r;
+  r.gb = (ctx->N + BLK - 1) / BLK;
+  r.gw = ctx->n_bnd ? (ctx->n_bnd + BLK - 1) / BLK : 0;
+  r.collide = ctx->adj_partial;
+  r.rho = ctx->adj_partial + (size_t)r.gb * NPAR;
+  r.wet = ctx->adj_partial + (size_t)2 * r.gb * NPAR;
+  return r;
+}
+
+// mu -> rho transpose, wetting part 1, and the output kernel shared by the
+// three entry points; lmu is the final adjoint of mu on fluid nodes
+void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R) {
+  const KParams &kp = ctx->kp;
+  cudaStream_t s = ctx->stream;
+  k_adj_rho<<<R.gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, lmu, R.rho, kp);
+  ctx->launches++;
+  if (ctx->n_bnd) {
+    k_adj_wet_prep<<<R.gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, R.wet, kp);
+    ctx->launches++;
+  }
+}
+
+// lmu: gather of lg (+ the local part), and Eq. 36 transposed with walls
+const float *adj_mu(lbm_ctx *ctx) {
+  const KParams &kp = ctx->kp;
+  const int g = (kp.N + 255) / 256;
+  k_adj_mu<<<g, 256, 0, ctx->stream>>>(ctx->mask, ctx->adj, kp);
+  ctx->launches++;
+  if (!ctx->mask) return ctx->adj.pm;
+  k_adj_wet_mu<<<g, 256, 0, ctx->stream>>>(ctx->mask, ctx->adj, kp);
+  ctx->launches++;
+  return ctx->adj.mu;
+}
+
 void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
-  const int gb = (kp.N + BLK - 1) / BLK, g = (kp.N + 255) / 256;
-  // fields of the initial density are in ctx->fld (launch_init ran before)
+  const int g = (kp.N + 255) / 256;
+  const Regions R = regions(ctx);
+  // fields of the initial density are in ctx->fld (lbm_set_state ran before)
   k_adj_init<<<g, 256, 0, s>>>(ctx->mask, u0, lam0, ctx->fld, ctx->adj, kp);
-  k_adj_rho<<<gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
-  k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
-  int launches = 3;
-  if (ctx->n_bnd) {
-    const int gw = (ctx->n_bnd + BLK - 1) / BLK;
-    k_adj_wet_prep<<<gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
-    k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gw, grad);
-    k_adj_wet_rho<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
-    launches += 3;
-  }
-  k_adj_grad_rho0<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, grad_rho0, kp);
-  ctx->launches += launches + 1;
+  ctx->launches++;
+  cudaMemsetAsync(R.collide, 0, (size_t)R.gb * NPAR * sizeof(double), s);
+  adj_tail(ctx, ctx->adj.mu, R);
+  k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
+  k_adj_grad_rho0<<<g, 256, 0, s>>>(ctx->mask, ctx->n_bnd ? 1 : 0, ctx->adj, grad_rho0, kp);
+  ctx->launches += 2;
 }
 
 void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
-  const int gb = (kp.N + BLK - 1) / BLK, g = (kp.N + 255) / 256;
+  const int g = (kp.N + 255) / 256;
+  const Regions R = regions(ctx);
   const float rl = (float)ctx->params.rho_l, rv = (float)ctx->params.rho_v;
   launch_fields_full(ctx);
-  k_obj_sums<<<gb, BLK, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj_partial, kp, rv);
-  k_obj_finish<<<1, 32, 0, s>>>(kind, ctx->adj_partial, gb, J, rl, rv);
+  k_obj_sums<<<R.gb, BLK, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj_partial, kp, rv);
+  k_obj_finish<<<1, RB, 0, s>>>(kind, ctx->adj_partial, R.gb, J, rl, rv);
   k_obj_seed<<<g, 256, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj, J, kp, rl, rv);
+  ctx->launches += 3;
   cudaMemsetAsync(lam, 0, 27 * (size_t)kp.N * sizeof(float), s);
   k_adj_fields<<<g, 256, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
-  k_adj_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
-  if (ctx->mask)
-    k_adj_wet_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
-  else
-    cudaMemcpyAsync(ctx->adj.mu, ctx->adj.pm, (size_t)kp.N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  ctx->launches++;
+  const float *lmu = adj_mu(ctx);
   // the objective's direct dependence on kappa and on the wetting value
-  k_adj_rho<<<gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
-  if (grad) k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
-  int launches = 9;
-  if (ctx->n_bnd) {
-    const int gw = (ctx->n_bnd + BLK - 1) / BLK;
-    k_adj_wet_prep<<<gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
-    if (grad) k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gw, grad);
-    k_adj_wet_rho<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
-    launches += 3;
+  cudaMemsetAsync(R.collide, 0, (size_t)R.gb * NPAR * sizeof(double), s);
+  adj_tail(ctx, lmu, R);
+  if (grad) {
+    k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
+    ctx->launches++;
   }
-  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, lam, kp);
-  ctx->launches += launches;
+  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->n_bnd ? 1 : 0, ctx->adj, lam, kp);
+  ctx->launches++;
 }
 
 void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
+  const int g = (kp.N + 255) / 256;
+  const Regions R = regions(ctx);
   // forward recompute of the fields of f(t) (the state is in ctx->f[cur])
   launch_fields_full(ctx);
-  const int gb = (kp.N + BLK - 1) / BLK, g = (kp.N + 255) / 256;
   if (ctx->storage == LBM_F16)
-    k_adj_collide<__half><<<gb, BLK, 0, s>>>((const __half *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
-                                            ctx->fld, ctx->adj, ctx->adj_partial, kp);
+    k_adj_collide<__half><<<R.gb, BLK, 0, s>>>((const __half *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
+                                              ctx->fld, ctx->adj, R.collide, kp);
   else
-    k_adj_collide<float><<<gb, BLK, 0, s>>>((const float *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
-                                           ctx->fld, ctx->adj, ctx->adj_partial, kp);
-  k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
-  k_adj_phi<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
+    k_adj_collide<float><<<R.gb, BLK, 0, s>>>((const float *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
+                                             ctx->fld, ctx->adj, R.collide, kp);
   k_adj_fields<<<g, 256, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
-  k_adj_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
-  if (ctx->mask) {
-    k_adj_wet_mu<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
-  } else {
-    cudaMemcpyAsync(ctx->adj.mu, ctx->adj.pm, (size_t)kp.N * sizeof(float), cudaMemcpyDeviceToDevice, s);
-  }
-  k_adj_rho<<<gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
-  k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gb, grad);
-  if (ctx->n_bnd) {
-    const int gw = (ctx->n_bnd + BLK - 1) / BLK;
-    k_adj_wet_prep<<<gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, ctx->adj_partial, kp);
-    k_adj_reduce<<<1, 32, 0, s>>>(ctx->adj_partial, gw, grad);
-    k_adj_wet_rho<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, kp);
-  }
-  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->adj, lam_t, kp);
-  ctx->launches += 9 + (ctx->n_bnd ? 3 : 0);
+  ctx->launches += 2;
+  const float *lmu = adj_mu(ctx);
+  adj_tail(ctx, lmu, R);
+  k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
+  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->n_bnd ? 1 : 0, ctx->adj, lam_t, kp);
+  ctx->launches += 2;
 }
 
 }  // namespace lbm

@@ -23,7 +23,8 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 //   boundary list   N ints
 //   reduction       RED_BLOCKS * 2 doubles
 //   status          2 ints
-//   adjoint         16 N floats, then ceil(N/128) * LBM_NGRAD doubles
+//   adjoint         16 N floats, then 3 regions of ceil(N/128)+1 blocks x
+//                   LBM_NGRAD doubles of gradient partials
 struct Layout {
   size_t f0, f1, fields, bnd, red, status, adj, adj_partial, total;
 };
@@ -42,7 +43,7 @@ bool layout(int nx, int ny, int nz, int storage, Layout *L) {
   L->red = off; off = align_up(off + (size_t)RED_BLOCKS * 2 * sizeof(double));
   L->status = off; off = align_up(off + 2 * sizeof(int));
   L->adj = off; off = align_up(off + 16 * (size_t)N * sizeof(float));
-  L->adj_partial = off; off = align_up(off + (size_t)((N + 127) / 128 + 1) * LBM_NGRAD * sizeof(double));
+  L->adj_partial = off; off = align_up(off + 3 * (size_t)((N + 127) / 128 + 1) * LBM_NGRAD * sizeof(double));
   L->total = off;
   return true;
 }
@@ -355,6 +356,51 @@ int lbm_adjoint_step(lbm_ctx *ctx, const void *state_t, const float *lam_next, f
   if (rc != LBM_OK) return rc;
   launch_adjoint_step(ctx, ctx->f[ctx->cur], lam_next, lam_t, grad_params);
   return check_cuda(ctx, "lbm_adjoint_step");
+}
+
+int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool, float *lam, float *lam_tmp,
+                        double *grad_params) {
+  if (!ctx || !ckpt || n < 1 || !state_pool || !lam || !lam_tmp || !grad_params || lam == lam_tmp)
+    return LBM_ERR_ARG;
+  if (!ctx->have_params) return fail(ctx, LBM_ERR_STATE, "lbm_set_params must come first");
+  const size_t pops = 27 * (size_t)ctx->N * (ctx->storage == LBM_F16 ? 2 : 4);
+  const bool rest = ctx->kp.shift_mode == LBM_SHIFT_REST;
+  const size_t sbb = rest ? 2 * (size_t)ctx->N * sizeof(float) : 0, sbytes = pops + sbb;
+  char *pool = (char *)state_pool;
+  cudaStream_t s = ctx->stream;
+  cudaGetLastError();
+  cudaMemcpyAsync(pool, ckpt, sbytes, cudaMemcpyDeviceToDevice, s);
+  if (rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + pops, sbb, cudaMemcpyDeviceToDevice, s);
+  void *own0 = ctx->f[0], *own1 = ctx->f[1];
+  const int own_cur = ctx->cur;
+  // recompute: step i reads pool[i-1] and writes pool[i]
+  for (int i = 1; i < n; ++i) {
+    ctx->f[ctx->cur] = pool + (size_t)(i - 1) * sbytes;
+    ctx->f[1 - ctx->cur] = pool + (size_t)i * sbytes;
+    launch_step(ctx);
+    if (rest)
+      cudaMemcpyAsync(pool + (size_t)i * sbytes + pops, ctx->fld.sb, sbb, cudaMemcpyDeviceToDevice, s);
+  }
+  // adjoint steps from t0+n-1 down to t0, lambda ping-pong
+  float *lin = lam, *lout = lam_tmp;
+  for (int k = n - 1; k >= 0; --k) {
+    ctx->f[ctx->cur] = pool + (size_t)k * sbytes;
+    if (rest) cudaMemcpyAsync(ctx->fld.sb, pool + (size_t)k * sbytes + pops, sbb, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
+    launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, grad_params);
+    float *t = lin;
+    lin = lout;
+    lout = t;
+  }
+  if (lin != lam) cudaMemcpyAsync(lam, lin, 27 * (size_t)ctx->N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  // the context's own buffers hold ckpt afterwards
+  ctx->f[0] = own0;
+  ctx->f[1] = own1;
+  ctx->cur = own_cur;
+  cudaMemcpyAsync(ctx->f[ctx->cur], ckpt, pops, cudaMemcpyDeviceToDevice, s);
+  if (rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + pops, sbb, cudaMemcpyDeviceToDevice, s);
+  ctx->have_state = 1;
+  return check_cuda(ctx, "lbm_adjoint_segment");
 }
 
 int lbm_adjoint_init(lbm_ctx *ctx, const float *rho0, const float *u0, const float *lam0, double *grad_params,

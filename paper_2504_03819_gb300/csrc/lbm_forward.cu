@@ -462,9 +462,12 @@ void launch_step_staged(lbm_ctx *ctx) {
 }
 
 void launch_fields_full(lbm_ctx *ctx) {
-  launch_fields(ctx, true);
-  k_q<<<blocks_for(ctx->N), BLOCK, 0, ctx->stream>>>(ctx->fld.phi, ctx->mask, ctx->fld.Q, ctx->kp);
-  ctx->launches++;
+  launch_moments_mu(ctx);
+  const Fields &d = ctx->fld;
+  const int g = blocks_for(ctx->N);
+  k_uphi<<<g, BLOCK, 0, ctx->stream>>>(d.rho, d.j, d.mu, ctx->mask, d.u, d.F, d.phi, ctx->kp);
+  k_q<<<g, BLOCK, 0, ctx->stream>>>(d.phi, ctx->mask, d.Q, ctx->kp);
+  ctx->launches += 2;
 }
 
 void launch_wet_rho(lbm_ctx *ctx) {

@@ -113,6 +113,7 @@ void launch_reduce(lbm_ctx *ctx, double *out);
 void launch_get_populations(lbm_ctx *ctx, float *out);
 void launch_copy_mu(lbm_ctx *ctx, float *out);       // mu' + mu_ref
 void launch_fields_full(lbm_ctx *ctx);               // rho, j, mu', u, F, phi, Q of the current state
+void launch_moments_mu(lbm_ctx *ctx);                // rho, j, mu' (+ wetting) of the current state
 void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad);
 void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0);
 void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad);

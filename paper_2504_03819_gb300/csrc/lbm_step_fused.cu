@@ -68,10 +68,10 @@ __global__ void __launch_bounds__(256) k_moments_v(const T *__restrict__ f, cons
 // chemical potential, z-marching (Eqs. 2, 32)
 // ---------------------------------------------------------------------------
 constexpr int MX = 32, MY = 8;   // tile of k_mu_z
-constexpr int MZ = 16;           // planes per block
+
 
 __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, const uint8_t *__restrict__ mask,
-                                                 float *__restrict__ mu, KParams kp) {
+                                                 float *__restrict__ mu, KParams kp, int MZ) {
   constexpr int HX = MX + 2, HY = MY + 2, HP = HX * HY;
   __shared__ float s_r[3][HP];
   const int tx = threadIdx.x % MX, ty = threadIdx.x / MX;
@@ -420,11 +420,45 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const T *__restrict__ fin, T *_
   }
 }
 
-constexpr int FUSED_TZ = 16;
+// planes per block of the z-marching kernels: the longest of 16, 8, 4, 2 that
+// still gives at least two blocks per SM (long columns amortise the halo
+// planes a block loads and computes before its first plane)
+int z_chunk(int xy_blocks, int nz) {
+  static int sms = 0;  // SM count of the device, read once
+  if (sms <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  for (int tz : {16, 8, 4, 2})
+    if ((long long)xy_blocks * ((nz + tz - 1) / tz) >= 2LL * sms) return tz;
+  return 1;
+}
 
 }  // namespace
 
 size_t fused_smem_bytes() { return sizeof(FusedSmem); }
+
+void launch_moments_mu(lbm_ctx *ctx) {
+  const KParams &kp = ctx->kp;
+  const Fields &d = ctx->fld;
+  cudaStream_t s = ctx->stream;
+  const int g = (kp.N + 255) / 256;
+  const void *fin = ctx->f[ctx->cur];
+  if (ctx->storage == LBM_F16)
+    k_moments_v<__half><<<g, 256, 0, s>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
+  else
+    k_moments_v<float><<<g, 256, 0, s>>>((const float *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
+  ctx->launches++;
+  if (ctx->n_bnd) launch_wet_rho(ctx);
+  const int xyb = ((kp.nx + MX - 1) / MX) * ((kp.ny + MY - 1) / MY);
+  const int mz = z_chunk(xyb, kp.nz);
+  dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + mz - 1) / mz);
+  k_mu_z<<<grid, MX * MY, 0, s>>>(d.rho, ctx->mask, d.mu, kp, mz);
+  ctx->launches++;
+  if (ctx->n_bnd) launch_wet_mu(ctx);
+}
 
 void launch_step_fused(lbm_ctx *ctx) {
   const KParams &kp = ctx->kp;
@@ -443,13 +477,17 @@ void launch_step_fused(lbm_ctx *ctx) {
   if (ctx->n_bnd) launch_wet_rho(ctx);
   {
     TimedLaunch t(ctx, K_MU);
-    dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + MZ - 1) / MZ);
-    k_mu_z<<<grid, MX * MY, 0, s>>>(d.rho, ctx->mask, d.mu, kp);
+    const int xyb = ((kp.nx + MX - 1) / MX) * ((kp.ny + MY - 1) / MY);
+    const int mz = z_chunk(xyb, kp.nz);
+    dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + mz - 1) / mz);
+    k_mu_z<<<grid, MX * MY, 0, s>>>(d.rho, ctx->mask, d.mu, kp, mz);
   }
   if (ctx->n_bnd) launch_wet_mu(ctx);
   {
     TimedLaunch t(ctx, K_COLLIDE);
-    dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + FUSED_TZ - 1) / FUSED_TZ);
+    const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
+    const int tz = z_chunk(xyb, kp.nz);
+    dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
     const size_t sm = sizeof(FusedSmem);
     static bool attr_set = false;  // the attribute is per function, set once per process
     if (!attr_set) {
@@ -459,10 +497,10 @@ void launch_step_fused(lbm_ctx *ctx) {
     }
     if (ctx->storage == LBM_F16) {
       k_fused<__half><<<grid, NT, sm, s>>>((const __half *)fin, (__half *)fout, ctx->mask, d.rho, d.j, d.mu, d.sb,
-                                           kp, FUSED_TZ);
+                                           kp, tz);
     } else {
       k_fused<float><<<grid, NT, sm, s>>>((const float *)fin, (float *)fout, ctx->mask, d.rho, d.j, d.mu, d.sb,
-                                          kp, FUSED_TZ);
+                                          kp, tz);
     }
   }
   ctx->cur = 1 - ctx->cur;
