@@ -311,8 +311,47 @@ def cpu_sample(nx: int, ny: int, nz: int, nsteps: int):
     return nx * ny * nz * nsteps / dt / 1e6, torch.get_num_threads(), dt
 
 
+def profile_case(name: str):
+    """Small runs for ncu captures (no timing): 'step128' = 4 steps of the
+    moving-droplet case on 128^3 (2.1 M nodes, state 0.23 GB > L2);
+    'adjoint64' = 4 adjoint steps of the 64^3 wall case."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2504_03819_gb300 import Domain, Params
+    from paper_2504_03819_gb300 import binding as Bd
+    from paper_2504_03819_gb300 import inputs as I
+    from paper_2504_03819_gb300.adjoint import rollout_gradient
+    __graft_entry__.build()
+    if name == "step128":
+        n = 128
+        om = [1.0] * 11
+        om[1] = 1.6
+        p = Params.vdw(9.0 / 49.0, 2.0 / 21.0, 1.0, 0.85, 0.01, omega=om)
+        d = Domain(n, n, n, "f32")
+        d.set_params(p)
+        d.set_state(torch.from_numpy(I.droplet(n, n, n, 16.0, p.rho_l, p.rho_v, width=2.0).astype(np.float32)),
+                    torch.from_numpy(I.uniform_velocity(n, n, n, (0.05, 0.02, 0.0)).astype(np.float32)))
+        d.step(4)
+        print("status", d.sync_status())
+    elif name == "adjoint64":
+        n = 64
+        p = Params.vdw(9.0 / 392.0, 2.0 / 21.0, 1.0, 0.85, 0.02, wetting_mode=Bd.WET_PHI, wetting_value=1.2)
+        mask = I.wall_mask(n, n, n, planes=(0, n - 1))
+        rho0 = torch.from_numpy(I.add_noise(I.sessile_droplet(n, n, n, 16.0, p.rho_l, p.rho_v), 1e-3,
+                                            seed=12345).astype(np.float32))
+        d = Domain(n, n, n, "f32", solid_mask=mask)
+        d.set_params(p)
+        J, g, _ = rollout_gradient(d, rho0, None, 4, 2, Bd.OBJ_CONTACT_RADIUS)
+        print("J", J)
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", default=None, help="run a small case for an ncu capture and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
@@ -320,6 +359,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
 

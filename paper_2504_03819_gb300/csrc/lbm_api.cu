@@ -233,6 +233,8 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
     k.ref_rho[i] = (float)refs[i];
     k.ref_omb[i] = (float)(1.0 - p->b * (double)(float)refs[i]);
     k.ref_dmu[i] = (float)(mu0((double)(float)refs[i]) - mu_ref);
+    k.ref_inv[i] = (float)(1.0 / (double)(float)refs[i]);
+    k.ref_bomb[i] = (float)(p->b / (1.0 - p->b * (double)(float)refs[i]));
   }
   ctx->have_params = 1;
   return LBM_OK;

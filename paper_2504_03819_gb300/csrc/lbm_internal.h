@@ -29,6 +29,7 @@ struct KParams {
   float mu_ref, pm_ref;             // pm_ref = (1 + mu_ref) / 3
   float rho_split;
   float ref_rho[2], ref_omb[2], ref_dmu[2];  // [0] vapour, [1] liquid: rho_r, 1 - b rho_r, mu0(rho_r) - mu_ref
+  float ref_inv[2], ref_bomb[2];             // 1 / rho_r, b / (1 - b rho_r)
 };
 
 // Device views carved out of the caller's workspace.

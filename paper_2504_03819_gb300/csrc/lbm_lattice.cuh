@@ -211,16 +211,17 @@ __device__ __forceinline__ void collide_cm(float k[27], float pm, float Fx, floa
 
 // Bulk chemical potential of the van der Waals EOS (bulk part of Eq. 32),
 // returned as mu0(rho) - mu_ref.  With d = rho - rho_r about the reference
-// density of the node's phase, the identity
-//   mu0(rho) = mu0(rho_r) + RT [ln(1 + d/rho_r) - ln(1 - b d/(1 - b rho_r))
-//              + b d / ((1 - b rho)(1 - b rho_r))] - 2 a d
+// density of the node's phase, A = d/rho_r and C = b d/(1 - b rho_r), the
+// identity
+//   mu0(rho) = mu0(rho_r) + RT [ln((1 + A)/(1 - C)) + C/(1 - b rho)] - 2 a d,
+//   ln((1 + A)/(1 - C)) = log1p((A + C)/(1 - C)),
 // holds exactly; every term is O(d), so FP32 keeps its relative precision
 // where the direct form cancels (liquid: RT(...) ~ 2.5 against 2 a rho ~ 2.3).
 __device__ __forceinline__ float mu0_vdw(float r, const KParams &kp) {
   const int ph = r > kp.rho_split ? 1 : 0;
-  const float rr = kp.ref_rho[ph], omb = kp.ref_omb[ph];
-  const float d = r - rr;
-  const float t = log1pf(d / rr) - log1pf(-kp.b * d / omb) + kp.b * d / ((1.0f - kp.b * r) * omb);
+  const float d = r - kp.ref_rho[ph];
+  const float A = d * kp.ref_inv[ph], Cc = d * kp.ref_bomb[ph];
+  const float t = log1pf((A + Cc) / (1.0f - Cc)) + Cc / (1.0f - kp.b * r);
   return kp.ref_dmu[ph] + kp.RT * t - 2.0f * kp.a * d;
 }
 

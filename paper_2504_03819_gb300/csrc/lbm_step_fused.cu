@@ -153,7 +153,17 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
 // ---------------------------------------------------------------------------
 // fused force / correction / collision / streaming
 // ---------------------------------------------------------------------------
-constexpr int TX = 32, TY = 8;  // column tile: one thread per (x, y)
+// column tile: one thread per (x, y); FUSED_MINB blocks per SM are requested
+#ifndef LBM_FUSED_TX
+#define LBM_FUSED_TX 32
+#endif
+#ifndef LBM_FUSED_TY
+#define LBM_FUSED_TY 8
+#endif
+#ifndef LBM_FUSED_MINB
+#define LBM_FUSED_MINB 2
+#endif
+constexpr int TX = LBM_FUSED_TX, TY = LBM_FUSED_TY;
 constexpr int NT = TX * TY;
 constexpr int H1X = TX + 2, H1Y = TY + 2, H1P = H1X * H1Y;  // one-node ring
 constexpr int H2X = TX + 4, H2Y = TY + 4, H2P = H2X * H2Y;  // two-node ring
@@ -176,7 +186,7 @@ __device__ __forceinline__ int r3(int z) { return (z + 6) % 3; }
 __device__ __forceinline__ int r2(int z) { return (z + 4) & 1; }
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 2) k_fused(const T *__restrict__ fin, T *__restrict__ fout,
+__global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restrict__ fin, T *__restrict__ fout,
                                                  const uint8_t *__restrict__ mask, const float *__restrict__ rho,
                                                  const float *__restrict__ jv, const float *__restrict__ mu,
                                                  float *__restrict__ sb, KParams kp, int TZ) {
