@@ -36,16 +36,20 @@ WORKLOAD_NAME = ("moving droplet 256^3 periodic, R=32 (tanh width 2), U=(0.05,0.
                  "T=0.85Tc, kappa=0.01, omega1=1.6, other rates 1")
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
-# storage, valid only while the kernel sources hash to `src`.
-NCU_TRAFFIC = {}
+# storage, valid only while the kernel sources hash to `src`.  The capture is
+# `--profile-case step128` (k_fused<float>, 128^3, 2,097,152 nodes): 290.99 MB
+# read + 197.46 MB written = 232.9 B per node, scaled by 8 to one 256^3 launch
+# (the kernel's traffic is proportional to the nodes it updates).
+NCU_TRAFFIC = {"f32": {"bytes_per_launch": 3907559424, "bytes_per_lu": 232.9,
+                       "captured_on": "128^3, scaled x8", "src": "6faabb8d8238f021"}}
 
 
 def src_hash() -> str:
+    """Hash of the sources the fused step kernel is compiled from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2504_03819_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ("lbm_step_fused.cu", "lbm_lattice.cuh", "lbm_internal.h"):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 

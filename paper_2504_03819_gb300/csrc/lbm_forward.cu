@@ -1,5 +1,6 @@
-// Forward time step of the free-energy D3Q27 LB model (Sec. II B, Sec. III C)
-// as a chain of kernels over structure-of-arrays fields:
+// Staged kernels of the free-energy D3Q27 LB model (Sec. II B, Sec. III C)
+// over structure-of-arrays fields, plus initialisation, boundary marking,
+// population import/export and the FP64 diagnostics:
 //
 //   moments   rho, j from the populations (Eq. 11) + status check
 //   wet_rho   solid-node density from the wetting scheme (Eqs. 37-38)
@@ -8,8 +9,10 @@
 //   uphi      F = (1/3 - rho) grad mu (Eq. 12), u = (j + F/2)/rho,
 //             phi = (p_m - rho/3) u with p_m = (1 + mu)/3
 //   q         Q_aa = -3 d_a phi_a (Eq. 27)
-//   collide   central-moment collision (Eqs. 19-26, 28) and push streaming
-//             with halfway bounce-back (Eq. 10, Sec. III C)
+//
+// The time step itself (collision and streaming) is the fused kernel chain
+// of lbm_step_fused.cu; these kernels produce the stored fields that
+// lbm_moments and the adjoint read.
 //
 // Stencils: lap g = 6 sum_i w_i (g(x+c_i) - g(x)), d_a g = 3 sum_i w_i c_ia
 // (g(x+c_i) - g(x)) (the subtracted centre value does not change the sum
@@ -189,66 +192,6 @@ __global__ void __launch_bounds__(BLOCK) k_q(const float *__restrict__ phi, cons
 }
 
 // ---------------------------------------------------------------------------
-// collision (Eqs. 19-26, 28) + push streaming with halfway bounce-back
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(BLOCK) k_collide(const T *__restrict__ fin, T *__restrict__ fout,
-                                                   const uint8_t *__restrict__ mask,
-                                                   const float *__restrict__ rho, const float *__restrict__ u,
-                                                   const float *__restrict__ F, const float *__restrict__ mu,
-                                                   const float *__restrict__ Q, float *__restrict__ sb,
-                                                   KParams kp) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N || (mask && mask[n])) return;
-  const size_t N = (size_t)kp.N;
-  const bool rest = kp.shift_mode == LBM_SHIFT_REST;
-  float f[27];
-  float rb = kp.rho_shift, cb = 0.0f;
-  if (rest) {
-    rb = sb[n];
-    cb = sb[N + n];
-  }
-#pragma unroll
-  for (int q = 0; q < 27; ++q)
-    f[q] = load_pop<T>(fin + q * N + n) + (rest ? shift_rest(q, rb, cb) : weight_of(q) * kp.rho_shift);
-  const float ux = u[n], uy = u[N + n], uz = u[2 * N + n];
-  const float Fx = F[n], Fy = F[N + n], Fz = F[2 * N + n];
-  const float Qx = Q[n], Qy = Q[N + n], Qz = Q[2 * N + n];
-  const float pm = pm_of(mu[n], kp);
-  float om1 = kp.om[1];
-  if (kp.nu > 0.0f) om1 = 1.0f / (rho[n] * kp.nu / pm + 0.5f);
-  to_central(f, ux, uy, uz);
-  collide_cm(f, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
-  from_central(f, ux, uy, uz);
-  Node p = decode(n, kp.nx, kp.ny);
-  // shifts are keyed by the destination node's fields of this step
-  const float r_own = rho[n], c_own = rest ? basis_c(r_own, mu[n], kp) : 0.0f;
-#pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    if (q == 13) {
-      store_pop<T>(fout + q * N + n, f[q] - (rest ? shift_rest(q, r_own, c_own) : weight_of(q) * kp.rho_shift));
-      continue;
-    }
-    int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
-    if (mask && mask[m]) {  // bounce back into x
-      store_pop<T>(fout + (size_t)(26 - q) * N + n,
-                   f[q] - (rest ? shift_rest(q, r_own, c_own) : weight_of(q) * kp.rho_shift));
-    } else {
-      float sh = weight_of(q) * kp.rho_shift;
-      if (rest) {
-        float rm = __ldg(rho + m);
-        sh = shift_rest(q, rm, basis_c(rm, __ldg(mu + m), kp));
-      }
-      store_pop<T>(fout + q * N + m, f[q] - sh);
-    }
-  }
-  if (rest) {
-    sb[n] = r_own;
-    sb[N + n] = c_own;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // initialisation: equilibrium central moments (Eq. 20) about u0
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(BLOCK) k_init_rho(const float *__restrict__ rho0, const uint8_t *__restrict__ mask,
@@ -407,24 +350,6 @@ __global__ void __launch_bounds__(RED_BLOCKS) k_reduce_final(const double *__res
 // host-side launch helpers
 // ---------------------------------------------------------------------------
 template <typename T>
-void step_impl(lbm_ctx *ctx) {
-  const KParams &kp = ctx->kp;
-  const Fields &d = ctx->fld;
-  const T *fin = (const T *)ctx->f[ctx->cur];
-  T *fout = (T *)ctx->f[1 - ctx->cur];
-  const int g = blocks_for(kp.N);
-  cudaStream_t s = ctx->stream;
-  { TimedLaunch t(ctx, K_MOMENTS); k_moments<T><<<g, BLOCK, 0, s>>>(fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp); }
-  if (ctx->n_bnd) { TimedLaunch t(ctx, K_WET_RHO); k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.rho, kp); }
-  { TimedLaunch t(ctx, K_MU); k_mu<<<g, BLOCK, 0, s>>>(d.rho, ctx->mask, d.mu, kp); }
-  if (ctx->n_bnd) { TimedLaunch t(ctx, K_WET_MU); k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.mu, kp); }
-  { TimedLaunch t(ctx, K_UPHI); k_uphi<<<g, BLOCK, 0, s>>>(d.rho, d.j, d.mu, ctx->mask, d.u, d.F, d.phi, kp); }
-  { TimedLaunch t(ctx, K_Q); k_q<<<g, BLOCK, 0, s>>>(d.phi, ctx->mask, d.Q, kp); }
-  { TimedLaunch t(ctx, K_COLLIDE); k_collide<T><<<g, BLOCK, 0, s>>>(fin, fout, ctx->mask, d.rho, d.u, d.F, d.mu, d.Q, d.sb, kp); }
-  ctx->cur = 1 - ctx->cur;
-}
-
-template <typename T>
 void fields_impl(lbm_ctx *ctx, bool with_u) {
   const KParams &kp = ctx->kp;
   const Fields &d = ctx->fld;
@@ -451,15 +376,6 @@ void launch_mark_boundary(lbm_ctx *ctx) {
 }
 
 void launch_step(lbm_ctx *ctx) { launch_step_fused(ctx); }
-
-// The seven-kernel form of the step (one kernel per stage, fields through
-// global memory).  Not on the lbm_step path; kept for stage-by-stage checks.
-void launch_step_staged(lbm_ctx *ctx) {
-  if (ctx->storage == LBM_F16)
-    step_impl<__half>(ctx);
-  else
-    step_impl<float>(ctx);
-}
 
 void launch_fields_full(lbm_ctx *ctx) {
   launch_moments_mu(ctx);

@@ -104,7 +104,6 @@ constexpr int STATUS_DOMAIN = 2;
 void launch_mark_boundary(lbm_ctx *ctx);
 void launch_step(lbm_ctx *ctx);                 // one full time step, swaps buffers
 void launch_step_fused(lbm_ctx *ctx);           // the three-kernel step (lbm_step_fused.cu)
-void launch_step_staged(lbm_ctx *ctx);          // the seven-kernel step (lbm_forward.cu)
 void launch_wet_rho(lbm_ctx *ctx);
 void launch_wet_mu(lbm_ctx *ctx);
 size_t fused_smem_bytes();
