@@ -49,7 +49,9 @@ enum {
   LBM_ERR_STATE = -3,      /* call out of order (no params / no state yet) */
   LBM_ERR_NONFINITE = -4,  /* a NaN/Inf density or momentum was detected */
   LBM_ERR_DOMAIN = -5,     /* a fluid density left (0, 1/b), the EOS domain */
-  LBM_ERR_SIZE = -6        /* workspace too small or grid too large */
+  LBM_ERR_SIZE = -6,       /* workspace too small or grid too large */
+  LBM_ERR_TIMEOUT = -7     /* a bounded wait inside a kernel gave up (an
+                              asynchronous copy did not complete in 2 s) */
 };
 
 /* Population storage type.  Compute is always FP32. */
@@ -154,9 +156,9 @@ int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0);
  */
 int lbm_step(lbm_ctx *ctx, int n);
 
-/* Synchronise the context's stream and return LBM_OK, LBM_ERR_NONFINITE or
- * LBM_ERR_DOMAIN from the device status word (the flags stay set until
- * lbm_set_state / lbm_set_raw_state / lbm_set_populations). */
+/* Synchronise the context's stream and return LBM_OK, LBM_ERR_NONFINITE,
+ * LBM_ERR_DOMAIN or LBM_ERR_TIMEOUT from the device status word (the flags
+ * stay set until lbm_set_state / lbm_set_raw_state / lbm_set_populations). */
 int lbm_sync_status(lbm_ctx *ctx);
 
 /*

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_NONFINITE, LBM_ERR_DOMAIN, LBM_ERR_SIZE = \
     0, -1, -2, -3, -4, -5, -6
+LBM_ERR_TIMEOUT = -7
 LBM_F32, LBM_F16 = 0, 1
 SHIFT_CONST, SHIFT_REST = 0, 1
 WET_NEUTRAL, WET_PHI, WET_DELTA = 0, 1, 2
@@ -22,7 +23,7 @@ OBJ_ENERGY, OBJ_CENTROID_X, OBJ_CONTACT_RADIUS = 0, 1, 2
 NGRAD = 13   # [kappa, omega_0 .. omega_10, wetting_value]
 ERROR_NAMES = {LBM_ERR_ARG: "LBM_ERR_ARG", LBM_ERR_CUDA: "LBM_ERR_CUDA", LBM_ERR_STATE: "LBM_ERR_STATE",
                LBM_ERR_NONFINITE: "LBM_ERR_NONFINITE", LBM_ERR_DOMAIN: "LBM_ERR_DOMAIN",
-               LBM_ERR_SIZE: "LBM_ERR_SIZE"}
+               LBM_ERR_SIZE: "LBM_ERR_SIZE", LBM_ERR_TIMEOUT: "LBM_ERR_TIMEOUT"}
 
 # Every symbol include/lbm.h declares, with (restype, argtypes).
 SIGNATURES = {

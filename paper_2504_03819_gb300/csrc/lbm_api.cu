@@ -269,6 +269,7 @@ int lbm_sync_status(lbm_ctx *ctx) {
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return check_cuda(ctx, "lbm_sync_status");
   if (st & STATUS_NONFINITE) return fail(ctx, LBM_ERR_NONFINITE, "non-finite density or momentum");
   if (st & STATUS_DOMAIN) return fail(ctx, LBM_ERR_DOMAIN, "density outside (0, 1/b)");
+  if (st & STATUS_TIMEOUT) return fail(ctx, LBM_ERR_TIMEOUT, "a kernel's bounded wait for a tensor copy gave up");
   return LBM_OK;
 }
 

@@ -2,6 +2,7 @@
 // kernels (lbm_forward.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -61,6 +62,15 @@ enum KernelId {
   K_COUNT
 };
 
+// Tensor map of one population buffer for the TMA-staged step, cached by
+// buffer address (the adjoint's segment sweep steps through pool buffers).
+struct TmapEntry {
+  const void *ptr;
+  int ok;  // 1: map encoded; 0: this buffer cannot be described (fallback)
+  CUtensorMap map;  // 64-byte aligned by its own declaration
+};
+constexpr int TMAP_CACHE = 4;
+
 struct ProfEvent {
   int id;
   cudaEvent_t start, stop;
@@ -90,6 +100,8 @@ struct lbm_ctx {
   std::vector<cudaEvent_t> prof_free;
   double prof_ms[lbm::K_COUNT];
   long long prof_n[lbm::K_COUNT];
+  lbm::TmapEntry tmaps[lbm::TMAP_CACHE];
+  int tmap_next;
   std::string err;
 };
 
@@ -98,6 +110,7 @@ namespace lbm {
 constexpr int RED_BLOCKS = 1024;
 constexpr int STATUS_NONFINITE = 1;
 constexpr int STATUS_DOMAIN = 2;
+constexpr int STATUS_TIMEOUT = 4;
 
 // Launchers (lbm_forward.cu).  Each enqueues on ctx->stream and counts its
 // launches; they do not check errors (the caller does).
@@ -106,7 +119,6 @@ void launch_step(lbm_ctx *ctx);                 // one full time step, swaps buf
 void launch_step_fused(lbm_ctx *ctx);           // the three-kernel step (lbm_step_fused.cu)
 void launch_wet_rho(lbm_ctx *ctx);
 void launch_wet_mu(lbm_ctx *ctx);
-size_t fused_smem_bytes();
 void launch_fields(lbm_ctx *ctx, bool with_u);  // moments .. (u, F, phi) of current state
 void launch_init(lbm_ctx *ctx, const float *rho0, const float *u0);
 void launch_reduce(lbm_ctx *ctx, double *out);

@@ -15,6 +15,10 @@
 // solid nodes.  Everything is FP32; shared-memory rings hold the planes a
 // stencil needs so each field value is read from global memory about once.
 #include "lbm_lattice.cuh"
+#include "lbm_tma.cuh"
+
+#include <atomic>
+#include <mutex>
 
 namespace lbm {
 
@@ -178,20 +182,38 @@ struct FusedSmem {
   float shift[3][4][H1P]; // storage shift by speed class, planes z-1 .. z+1
   float uF[2][6][NT];     // u, F of the tile for planes z, z+1
   uint8_t solid[4][H1P];  // mask planes
+  alignas(8) uint64_t bar;  // completion barrier of the population tile copy
 };
+// the population tile of one plane, [q][y][x], staged by a tensor copy
+// behind FusedSmem at a 128-byte boundary
+constexpr size_t FBUF_OFFSET = (sizeof(FusedSmem) + 127) / 128 * 128;
+template <typename T> constexpr size_t fused_smem_size(bool tma) {
+  return tma ? FBUF_OFFSET + 27 * NT * sizeof(T) : sizeof(FusedSmem);
+}
 
 __device__ __forceinline__ int r5(int z) { return (z + 10) % 5; }  // z >= -2
 __device__ __forceinline__ int r4(int z) { return (z + 8) & 3; }
 __device__ __forceinline__ int r3(int z) { return (z + 6) % 3; }
 __device__ __forceinline__ int r2(int z) { return (z + 4) & 1; }
 
-template <typename T>
-__global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restrict__ fin, T *__restrict__ fout,
-                                                 const uint8_t *__restrict__ mask, const float *__restrict__ rho,
-                                                 const float *__restrict__ jv, const float *__restrict__ mu,
-                                                 float *__restrict__ sb, KParams kp, int TZ) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+
+// MASK: the domain has solid nodes (bounce-back and solid checks compiled
+// in).  TMA: the populations of each plane arrive in shared memory by one
+// tensor copy issued a plane ahead (tmap describes fin as [27][nz][ny][nx]);
+// otherwise each thread loads its node's populations directly.
+template <typename T, bool MASK, bool TMA>
+__global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
+    k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
+            const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
+            float *__restrict__ sb, int *__restrict__ status, KParams kp, int TZ,
+            const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
+  const T *fbuf = reinterpret_cast<const T *>(smem_raw + FBUF_OFFSET);
+  constexpr uint32_t FBYTES = 27 * NT * sizeof(T);
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -200,6 +222,17 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restric
   const int nxy = nx * ny;
   const size_t N = (size_t)kp.N;
   const bool rest = kp.shift_mode == LBM_SHIFT_REST;
+
+  if (TMA) {
+    // the first plane's copy is in flight while the field planes load
+    if (tid == 0) {
+      tma_prefetch_map(&tmap);
+      mbar_init(&S.bar, 1);
+      mbar_fence_init();
+      mbar_arrive_expect_tx(&S.bar, FBYTES);
+      tma_load_4d(smem_raw + FBUF_OFFSET, &tmap, &S.bar, x0, y0, z0, 0);
+    }
+  }
 
   // xy offsets (periodic) of this thread's slots in the two-node and the
   // one-node rings; fixed for the whole column
@@ -232,7 +265,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restric
       pj[0][s] = ok ? __ldg(jv + g) : 0.0f;
       pj[1][s] = ok ? __ldg(jv + N + g) : 0.0f;
       pj[2][s] = ok ? __ldg(jv + 2 * N + g) : 0.0f;
-      psolid[s] = (ok && mask) ? mask[g] : (uint8_t)0;
+      if (MASK) psolid[s] = (ok && mask) ? mask[g] : (uint8_t)0;
     }
   };
   auto store = [&](int zm, int zr) {
@@ -249,7 +282,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restric
         S.j[rg][0][k] = pj[0][s];
         S.j[rg][1][k] = pj[1][s];
         S.j[rg][2][k] = pj[2][s];
-        S.solid[rg][k] = psolid[s];
+        if (MASK) S.solid[rg][k] = psolid[s];
       }
     }
   };
@@ -262,27 +295,28 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restric
       const int hx = k % H1X, hy = k / H1X;
       float phx = 0.0f, phy = 0.0f, phz = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f, Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
       float sh0 = 0.0f, sh1 = 0.0f, sh2 = 0.0f, sh3 = 0.0f;
-      if (!S.solid[rg][k]) {
+      if (!MASK || !S.solid[rg][k]) {
         const int c = (hy + 1) * H2X + hx + 1;  // position in the two-node ring
         const float mc = m1[c];
-        // sum_q w_q c_q mu'(x + c_q): sum_q w_q c_q = 0 makes the centre term
-        // drop out, and mu' is a small deviation, so no centring is needed
-        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+        // sum_q w_q c_q mu'(x + c_q), one partial sum per plane and axis so
+        // the dependent chains stay short (sum_q w_q c_q = 0: the centre
+        // term drops out, and mu' is a small deviation, so no centring)
+        float gx[3] = {0.0f, 0.0f, 0.0f}, gy[3] = {0.0f, 0.0f, 0.0f}, gz[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
           if (q == 13) continue;
           const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
           const float *pl = cz < 0 ? m0 : (cz == 0 ? m1 : m2);
           const float v = pl[c + cx + cy * H2X];
-          if (cx) gx = fmaf(cx * weight_of(q), v, gx);
-          if (cy) gy = fmaf(cy * weight_of(q), v, gy);
-          if (cz) gz = fmaf(cz * weight_of(q), v, gz);
+          if (cx) gx[cz + 1] = fmaf(cx * weight_of(q), v, gx[cz + 1]);
+          if (cy) gy[cz + 1] = fmaf(cy * weight_of(q), v, gy[cz + 1]);
+          if (cz) gz[cz + 1] = fmaf(cz * weight_of(q), v, gz[cz + 1]);
         }
         const float r = S.rho[rg][k];
         const float cf = 3.0f * (1.0f / 3.0f - r);
-        Fx = cf * gx;
-        Fy = cf * gy;
-        Fz = cf * gz;
+        Fx = cf * ((gx[0] + gx[2]) + gx[1]);
+        Fy = cf * ((gy[0] + gy[2]) + gy[1]);
+        Fz = cf * (gz[0] + gz[2]);
         const float ir = 1.0f / r;
         ux = (S.j[rg][0][k] + 0.5f * Fx) * ir;
         uy = (S.j[rg][1][k] + 0.5f * Fy) * ir;
@@ -342,47 +376,66 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restric
   fields(z0 - 1, false);
   fields(z0, true);
 
+  const int c1 = (ty + 1) * H1X + tx + 1;
   for (int z = z0; z < z1; ++z) {
     // publish mu'(z+2), rho/j(z+1); prefetch mu'(z+3), rho/j(z+2)
     store(z + 2, z + 1);
     if (z + 1 < z1) fetch(z + 3, z + 2);
     // populations of this node
     const int n = x + nx * y + nxy * z;
-    const bool active = inside && !(S.solid[r4(z)][(ty + 1) * H1X + tx + 1]);
+    const bool active = inside && (!MASK || !S.solid[r4(z)][c1]);
     float f[27];
     float rb = kp.rho_shift, cb = 0.0f;
-    if (active) {
-#pragma unroll
-      for (int q = 0; q < 27; ++q) f[q] = load_pop<T>(fin + q * N + n);
-      if (rest) {
-        rb = sb[n];
-        cb = sb[N + n];
-      }
+    if (rest && active) {
+      rb = sb[n];
+      cb = sb[N + n];
     }
-    __syncthreads();
+    if (TMA) {
+      const bool ok = mbar_wait_bounded(&S.bar, (uint32_t)(z - z0) & 1u);
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) f[q] = to_f32<T>(fbuf[q * NT + tid]);
+      }
+      // every thread has its populations: the buffer takes the next plane
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(status, STATUS_TIMEOUT);
+          mbar_wait_bounded(&S.bar, (uint32_t)(z - z0) & 1u);  // let the late copy land before exit
+        }
+        return;
+      }
+      if (tid == 0 && z + 1 < z1) {
+        mbar_arrive_expect_tx(&S.bar, FBYTES);
+        tma_load_4d(smem_raw + FBUF_OFFSET, &tmap, &S.bar, x0, y0, z + 1, 0);
+      }
+    } else {
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) f[q] = load_pop<T>(fin + q * N + n);
+      }
+      __syncthreads();
+    }
     fields(z + 1, true);
     __syncthreads();
     if (!active) continue;
 
-    // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa (phi_a(x + c_q) - phi_a(x))
-    const int c1 = (ty + 1) * H1X + tx + 1;
+    // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa phi_a(x + c_q), partial sums
+    // per plane
     const float *p0 = S.phi[r3(z - 1)][0], *p1 = S.phi[r3(z)][0], *p2 = S.phi[r3(z + 1)][0];
-    float Qx = 0.0f, Qy = 0.0f, Qz = 0.0f;
-    {
+    float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f}, qz[2] = {0.0f, 0.0f};
 #pragma unroll
-      for (int q = 0; q < 27; ++q) {
-        if (q == 13) continue;
-        const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
-        const float *pl = cz < 0 ? p0 : (cz == 0 ? p1 : p2);
-        const int o = c1 + cx + cy * H1X;
-        if (cx) Qx = fmaf(cx * weight_of(q), pl[o], Qx);
-        if (cy) Qy = fmaf(cy * weight_of(q), pl[H1P + o], Qy);
-        if (cz) Qz = fmaf(cz * weight_of(q), pl[2 * H1P + o], Qz);
-      }
-      Qx *= -9.0f;
-      Qy *= -9.0f;
-      Qz *= -9.0f;
+    for (int q = 0; q < 27; ++q) {
+      if (q == 13) continue;
+      const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
+      const float *pl = cz < 0 ? p0 : (cz == 0 ? p1 : p2);
+      const int o = c1 + cx + cy * H1X;
+      if (cx) qx[cz + 1] = fmaf(cx * weight_of(q), pl[o], qx[cz + 1]);
+      if (cy) qy[cz + 1] = fmaf(cy * weight_of(q), pl[H1P + o], qy[cz + 1]);
+      if (cz) qz[cz > 0] = fmaf(cz * weight_of(q), pl[2 * H1P + o], qz[cz > 0]);
     }
+    const float Qx = -9.0f * ((qx[0] + qx[2]) + qx[1]);
+    const float Qy = -9.0f * ((qy[0] + qy[2]) + qy[1]);
+    const float Qz = -9.0f * (qz[0] + qz[1]);
     const float *uF = S.uF[r2(z)][0];
     const int t = ty * TX + tx;
     const float ux = uF[t], uy = uF[NT + t], uz = uF[2 * NT + t];
@@ -402,7 +455,6 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restric
     // push with bounce-back; shifts keyed by the destination's fields
     const int oz[3] = {z == 0 ? (nz - 1) * nxy : -nxy, 0, z == nz - 1 ? -(nz - 1) * nxy : nxy};
     const float c_own = rest ? basis_c(r_own, mu_own, kp) : 0.0f;
-    const bool has_mask = mask != nullptr;
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
       const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
@@ -413,8 +465,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB) k_fused(const T *__restric
         continue;
       }
       const int hk = c1 + cx + cy * H1X;
-      const int rg = r4(z + cz);
-      if (has_mask && S.solid[rg][hk]) {
+      if (MASK && S.solid[r4(z + cz)][hk]) {
         if (rest) sh = shift_rest(q, r_own, c_own);
         store_pop<T>(fout + (size_t)(26 - q) * N + n, f[q] - sh);
       } else {
@@ -446,9 +497,98 @@ int z_chunk(int xy_blocks, int nz) {
   return 1;
 }
 
-}  // namespace
+// The dynamic shared-memory limit is a per-device attribute of each kernel:
+// raised once per device for every instantiation that is launched.
+template <auto K> void ensure_smem(size_t bytes) {
+  static std::atomic<unsigned long long> done{0};  // one bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load() & bit)) {
+    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done.fetch_or(bit);
+  }
+}
 
-size_t fused_smem_bytes() { return sizeof(FusedSmem); }
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of population buffer p as [27][nz][ny][nx] with a box of one
+// tile plane (TX x TY x 1 x 27), or nullptr when p cannot be described: the
+// rows must be multiples of 16 bytes (nx a multiple of 4 in FP32, 8 in FP16)
+// and p 16-byte aligned.  Encoded maps are cached in the context by address.
+const CUtensorMap *population_tmap(lbm_ctx *ctx, const void *p) {
+  for (const TmapEntry &e : ctx->tmaps)
+    if (e.ptr == p) return e.ok ? &e.map : nullptr;
+  TmapEntry &e = ctx->tmaps[ctx->tmap_next];
+  ctx->tmap_next = (ctx->tmap_next + 1) % TMAP_CACHE;
+  e.ptr = p;
+  e.ok = 0;
+  const size_t es = ctx->storage == LBM_F16 ? 2 : 4;
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn || reinterpret_cast<uintptr_t>(p) % 16 != 0 || ((size_t)ctx->nx * es) % 16 != 0) return nullptr;
+  const cuuint64_t dims[4] = {(cuuint64_t)ctx->nx, (cuuint64_t)ctx->ny, (cuuint64_t)ctx->nz, 27};
+  const cuuint64_t strides[3] = {ctx->nx * es, (cuuint64_t)ctx->nx * ctx->ny * es, (cuuint64_t)ctx->N * es};
+  const cuuint32_t box[4] = {TX, TY, 1, 27};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(&e.map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                        const_cast<void *>(p), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  e.ok = r == CUDA_SUCCESS;
+  return e.ok ? &e.map : nullptr;
+}
+
+template <typename T>
+void launch_fused(lbm_ctx *ctx, const void *fin_v, void *fout_v) {
+  const KParams &kp = ctx->kp;
+  const Fields &d = ctx->fld;
+  const T *fin = static_cast<const T *>(fin_v);
+  T *fout = static_cast<T *>(fout_v);
+  const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
+  const int tz = z_chunk(xyb, kp.nz);
+  const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
+  const CUtensorMap *map = population_tmap(ctx, fin_v);
+  cudaStream_t s = ctx->stream;
+  if (map) {
+    constexpr size_t sm = fused_smem_size<T>(true);
+    if (ctx->mask) {
+      ensure_smem<k_fused<T, true, true>>(sm);
+      k_fused<T, true, true><<<grid, NT, sm, s>>>(fin, fout, ctx->mask, d.rho, d.j, d.mu, d.sb, ctx->status, kp, tz,
+                                                  *map);
+    } else {
+      ensure_smem<k_fused<T, false, true>>(sm);
+      k_fused<T, false, true><<<grid, NT, sm, s>>>(fin, fout, nullptr, d.rho, d.j, d.mu, d.sb, ctx->status, kp, tz,
+                                                   *map);
+    }
+  } else {
+    // rows that a tensor copy cannot describe: per-thread loads, the mask
+    // checks compiled in (an all-fluid domain has an all-zero solid plane)
+    constexpr size_t sm = fused_smem_size<T>(false);
+    static const CUtensorMap unused{};
+    ensure_smem<k_fused<T, true, false>>(sm);
+    k_fused<T, true, false><<<grid, NT, sm, s>>>(fin, fout, ctx->mask, d.rho, d.j, d.mu, d.sb, ctx->status, kp, tz,
+                                                 unused);
+  }
+}
+
+}  // namespace
 
 void launch_moments_mu(lbm_ctx *ctx) {
   const KParams &kp = ctx->kp;
@@ -495,23 +635,10 @@ void launch_step_fused(lbm_ctx *ctx) {
   if (ctx->n_bnd) launch_wet_mu(ctx);
   {
     TimedLaunch t(ctx, K_COLLIDE);
-    const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
-    const int tz = z_chunk(xyb, kp.nz);
-    dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
-    const size_t sm = sizeof(FusedSmem);
-    static bool attr_set = false;  // the attribute is per function, set once per process
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_fused<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr_set = true;
-    }
-    if (ctx->storage == LBM_F16) {
-      k_fused<__half><<<grid, NT, sm, s>>>((const __half *)fin, (__half *)fout, ctx->mask, d.rho, d.j, d.mu, d.sb,
-                                           kp, tz);
-    } else {
-      k_fused<float><<<grid, NT, sm, s>>>((const float *)fin, (float *)fout, ctx->mask, d.rho, d.j, d.mu, d.sb,
-                                          kp, tz);
-    }
+    if (ctx->storage == LBM_F16)
+      launch_fused<__half>(ctx, fin, fout);
+    else
+      launch_fused<float>(ctx, fin, fout);
   }
   ctx->cur = 1 - ctx->cur;
 }

@@ -79,9 +79,11 @@ def add_noise(rho: np.ndarray, sigma: float, seed: int = 12345) -> np.ndarray:
 
 
 def random_populations(nx: int, ny: int, nz: int, seed: int, scale: float = 0.05,
-                       base: np.ndarray | None = None) -> np.ndarray:
+                       base: np.ndarray | None = None, dtype=np.float64) -> np.ndarray:
     """Seeded random perturbation field of shape (27, nz, ny, nx), optionally
-    added to a base population field (for non-equilibrium test states)."""
+    added to a base population field (for non-equilibrium test states).
+    dtype=np.float32 draws FP32 normals directly (full-size fields)."""
     rng = np.random.default_rng(seed)
-    pert = scale * rng.standard_normal((27, nz, ny, nx))
+    pert = rng.standard_normal((27, nz, ny, nx), dtype=dtype)
+    pert *= dtype(scale) if dtype is np.float32 else scale
     return pert if base is None else base + pert

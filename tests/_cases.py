@@ -49,6 +49,12 @@ CASES = {
     "wall_neutral_rates_noq4": dict(n=(9, 9, 10), walls=(0,), radius=3.5, sessile=True, u=(0.0, 0.01, 0.0),
                                     p=dict(q4_correction=0,
                                            omega=[1.0, 1.6, 1.2, 0.9, 1.1, 1.3, 0.8, 1.4, 1.05, 0.95, 1.5])),
+    # rows of 16-byte multiples (tensor-copy staging of the population
+    # tiles): two tiles in x and y with ragged tails, periodic (FP16 too)
+    "droplet_tiles": dict(n=(40, 12, 10), walls=(), radius=4.0, u=(0.02, 0.01, -0.01), p={}),
+    # the same staging with walls and hydrophilic wetting (FP32 rows only)
+    "wall_tiles": dict(n=(36, 10, 9), walls=(0, 8), radius=3.5, sessile=True, u=(0.01, 0.0, 0.0),
+                       p=dict(wetting_mode=1, wetting_value=1.2)),
     # paper EOS, 0.7 T_c, kappa = 0.02, degenerate 1 x 1 x n flat interface
     "flat_paper_1d": dict(n=(1, 1, 48), walls=(), slab=24, u=(0.0, 0.0, 0.0),
                           p=dict(a=A392, t=0.7, kappa=0.02, nu=0.15)),

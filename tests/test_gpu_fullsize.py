@@ -1,0 +1,116 @@
+"""Parity at the workloads' full sizes, in the launch configuration the bench
+times: the 256^3 moving-droplet case (a = 9/49, kappa = 0.01, 0.85 T_c,
+omega_1 = 1.6; FP32 and FP16 storage) and the 256 x 256 x 128 wall case
+(solid planes z = 0 and z = 127, hydrophilic wetting).
+
+The oracle cannot step these domains, so outputs are sampled: one step of
+the model moves information at most four nodes (a population at x comes from
+the collision at x - c_q, which reads rho up to three nodes further through
+mu, grad mu, phi and Q; next to walls the wetting averages add one node per
+stage), so the oracle steps a periodic sub-box of half-width R around each
+sampled node, cut from the same input, and its centre must equal the GPU's
+value.  Samples include tile edges and corners (32 x 8 columns) and the
+first and last planes of the z chunks of the fused kernel.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lattice as L
+from oracle import step as S
+from paper_2504_03819_gb300 import Domain
+from paper_2504_03819_gb300 import inputs as I
+
+from _cases import oracle_params, vdw
+
+pytestmark = pytest.mark.gpu
+
+
+def seeded_state(rho: np.ndarray, seed: int, solid: np.ndarray | None = None) -> torch.Tensor:
+    """f_q = w_q rho (1 + 0.01 xi_q), xi ~ N(0, 1) seeded: FP32, zero on
+    solid nodes; the same array feeds the GPU and the oracle's sub-boxes."""
+    nz, ny, nx = rho.shape
+    w = L.weights().numpy().astype(np.float32)
+    f = I.random_populations(nx, ny, nz, seed, scale=0.01, dtype=np.float32)
+    f += np.float32(1.0)
+    f *= rho.astype(np.float32)[None]
+    f *= w[:, None, None, None]
+    if solid is not None:
+        f[:, solid] = 0.0
+    return torch.from_numpy(f)
+
+
+def samples(n, rng, extra):
+    """Tile-edge / chunk-edge positions plus seeded random ones, as (x, y, z)."""
+    nx, ny, nz = n
+    edge_x = [0, 31, 32, nx - 1]
+    edge_y = [0, 7, 8, ny - 1]
+    edge_z = [0, 15, 16, nz - 1]
+    pts = [(edge_x[i % 4], edge_y[(i // 4) % 4], edge_z[(i * 3 + i // 4) % 4]) for i in range(16)]
+    pts += [tuple(int(v) for v in rng.integers(0, (nx, ny, nz))) for _ in range(extra)]
+    return pts
+
+
+def sub_box(a: torch.Tensor, x, y, z, R):
+    """Periodic sub-array a[..., z-R:z+R+1, y-R:y+R+1, x-R:x+R+1]."""
+    nz, ny, nx = a.shape[-3:]
+    iz = torch.arange(z - R, z + R + 1) % nz
+    iy = torch.arange(y - R, y + R + 1) % ny
+    ix = torch.arange(x - R, x + R + 1) % nx
+    return a[..., iz, :, :][..., iy, :][..., ix]
+
+
+def check_sampled(d, f, solid, p, pts, R, tol):
+    d.set_populations(f)
+    d.step(1)
+    assert d.sync_status() == 0
+    got = d.get_populations().cpu()
+    op = oracle_params(p)
+    scale = float(f.abs().max())
+    worst = 0.0
+    for (x, y, z) in pts:
+        fs = sub_box(f, x, y, z, R).double()
+        ss = sub_box(solid, x, y, z, R)
+        if bool(ss[R, R, R]):
+            continue
+        ref = S.step(fs, ss, op)[:, R, R, R]
+        err = float((got[:, z, y, x].double() - ref).abs().max()) / scale
+        worst = max(worst, err)
+        assert err < tol, ((x, y, z), err)
+    return worst
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 2e-6), ("f16", 1e-4)])
+def test_moving_droplet_256_sampled(storage, tol):
+    n = 256
+    om = [1.0] * 11
+    om[1] = 1.6
+    p = vdw(omega=om)
+    rho = I.droplet(n, n, n, 32.0, p.rho_l, p.rho_v, width=2.0)
+    f = seeded_state(rho, seed=2024)
+    d = Domain(n, n, n, storage)
+    d.set_params(p)
+    solid = torch.zeros(n, n, n, dtype=torch.bool)
+    pts = samples((n, n, n), np.random.default_rng(7), 16)
+    # droplet surface nodes (the largest forces and corrections)
+    pts += [(128 + 32, 128, 128), (128, 96, 128), (150, 150, 105), (127, 127, 160)]
+    check_sampled(d, f, solid, p, pts, R=4, tol=tol)
+    d.close()
+
+
+def test_wall_256x256x128_sampled():
+    nx, ny, nz = 256, 256, 128
+    p = vdw(wetting_mode=1, wetting_value=1.2)
+    mask = I.wall_mask(nx, ny, nz, planes=(0, nz - 1))
+    rho = I.sessile_droplet(nx, ny, nz, 40.0, p.rho_l, p.rho_v, wall_z=0.5)
+    f = seeded_state(rho, seed=77, solid=mask.astype(bool))
+    d = Domain(nx, ny, nz, "f32", solid_mask=mask)
+    d.set_params(p)
+    solid = torch.from_numpy(mask.astype(bool))
+    rng = np.random.default_rng(9)
+    pts = samples((nx, ny, nz), rng, 8)
+    # fluid nodes next to both walls, under the droplet and at its contact line
+    pts += [(128, 128, 1), (128, 128, 2), (168, 128, 1), (90, 128, 1), (10, 250, 1), (128, 128, nz - 2),
+            (40, 30, nz - 3)]
+    check_sampled(d, f, solid, p, pts, R=7, tol=2e-6)
+    d.close()

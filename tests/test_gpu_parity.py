@@ -157,8 +157,9 @@ def test_constant_shift_mode_fifty_steps(name):
     assert absd(m["u"], ref["u"]) < 1e-6
 
 
-def test_fp16_storage_fifty_steps():
-    case = build("droplet_periodic")
+@pytest.mark.parametrize("name", ["droplet_periodic", "droplet_tiles"])
+def test_fp16_storage_fifty_steps(name):
+    case = build(name)
     p = case["p"]
     d = gpu(case, "f16")
     d.set_state(torch.from_numpy(case["rho0"]).float(), torch.from_numpy(case["u0"]).float())
