@@ -293,7 +293,7 @@ const char *lbm_kernel_name(int id);
  *
  * Runs the same kernels as lbm_step with LBM_F32 storage on unshifted
  * populations (params->shift_mode and rho_shift are ignored).  The step's
- * scratch (the macroscopic fields and the boundary list, about 2.6 MB) lives
+ * scratch (the macroscopic fields and the wall bookkeeping, about 2.9 MB) lives
  * in one static device array of the library, sized for
  * LBM_NOALLOC_MAX_NODES nodes; every GPU that loads the library holds it
  * until the process exits.

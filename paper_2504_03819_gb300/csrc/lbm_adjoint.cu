@@ -281,35 +281,74 @@ __device__ __forceinline__ void collide_vjp(const float *k, float *ls, float *lk
   gom[10] += (-KM(2, 2, 2) + pm * cs2 * cs2) * LS(2, 2, 2);
 }
 
-// block sum of NPAR floats (as doubles) into partial[blockIdx.x * NPAR + i]
+// A node of a 3-D launch: blocks of 32 x blockDim.y threads over (x, y), one
+// z-plane per block row of the grid; neighbour indices by periodic offsets.
+struct Site {
+  int n;
+  bool in;
+  int ox[3], oy[3], oz[3];
+  __device__ __forceinline__ int at(int cx, int cy, int cz) const { return n + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]; }
+};
+
+__device__ __forceinline__ Site site_of(const KParams &kp) {
+  Site s;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz, nxy = nx * ny;
+  s.in = x < nx && y < ny;
+  s.n = x + nx * (y + ny * z);
+  s.ox[0] = x == 0 ? nx - 1 : -1;
+  s.ox[1] = 0;
+  s.ox[2] = x == nx - 1 ? -(nx - 1) : 1;
+  s.oy[0] = y == 0 ? (ny - 1) * nx : -nx;
+  s.oy[1] = 0;
+  s.oy[2] = y == ny - 1 ? -(ny - 1) * nx : nx;
+  s.oz[0] = z == 0 ? (nz - 1) * nxy : -nxy;
+  s.oz[1] = 0;
+  s.oz[2] = z == nz - 1 ? -(nz - 1) * nxy : nxy;
+  return s;
+}
+
+__device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
+
+// block sum of NPAR values into partial[block_id() * NPAR + i]: a shuffle
+// tree per warp, then the warps in order (fixed order: deterministic)
 __device__ void block_partials(double v[NPAR], double *partial) {
-  __shared__ double sm[NPAR][BLK];
+  constexpr int MAXW = 8;
+  __shared__ double sm[NPAR][MAXW];
+  const int t = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nw = (blockDim.x * blockDim.y) / 32;
 #pragma unroll
-  for (int i = 0; i < NPAR; ++i) sm[i][threadIdx.x] = v[i];
+  for (int i = 0; i < NPAR; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+  if ((t & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < NPAR; ++i) sm[i][t >> 5] = v[i];
   __syncthreads();
-  for (int s = BLK / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-#pragma unroll
-      for (int i = 0; i < NPAR; ++i) sm[i][threadIdx.x] += sm[i][threadIdx.x + s];
-    __syncthreads();
+  if (t < NPAR) {
+    double acc = 0.0;
+    for (int w = 0; w < nw; ++w) acc += sm[t][w];
+    partial[(size_t)block_id() * NPAR + t] = acc;
   }
-  if (threadIdx.x < NPAR) partial[(size_t)blockIdx.x * NPAR + threadIdx.x] = sm[threadIdx.x][0];
 }
 
 // ---------------------------------------------------------------------------
 // collision + streaming adjoint, per fluid node
 // ---------------------------------------------------------------------------
+// three blocks per SM for FP32 storage; the FP16 conversions need the
+// register budget of two
 template <typename T>
-__global__ void __launch_bounds__(BLK, 3) k_adj_collide(const T *__restrict__ fstate, const float *__restrict__ sb,
-                                                     const uint8_t *__restrict__ mask,
+__global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(const T *__restrict__ fstate, const float *__restrict__ sb,
+                                                     const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
                                                      const float *__restrict__ lam_next, float *__restrict__ lam_t,
                                                      Fields d, AdjFields a, double *__restrict__ partial, KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const Site st = site_of(kp);
+  const int n = st.n;
   double par[NPAR];
 #pragma unroll
   for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
   const size_t N = (size_t)kp.N;
-  if (n < kp.N) {
+  if (st.in) {
     if (mask && mask[n]) {
 #pragma unroll
       for (int q = 0; q < 27; ++q) lam_t[q * N + n] = 0.0f;
@@ -326,6 +365,18 @@ __global__ void __launch_bounds__(BLK, 3) k_adj_collide(const T *__restrict__ fs
         for (int q = 0; q < 27; ++q)
           f[q] = load_pop<T>(fstate + q * N + n) + (rest ? shift_rest(q, rb, cb) : weight_of(q) * rb);
       };
+      // pull of lambda(t+1): transpose of push with bounce-back
+      const uint32_t solid = mask ? nbr[n] : 0u;
+      float lam[27];
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        if (q == 13) {
+          lam[q] = lam_next[q * N + n];
+          continue;
+        }
+        lam[q] = ((solid >> q) & 1u) ? lam_next[(size_t)(26 - q) * N + n]
+                                     : lam_next[q * N + st.at(cx_of(q), cy_of(q), cz_of(q))];
+      }
       const float ux = d.u[n], uy = d.u[N + n], uz = d.u[2 * N + n];
       const float Fx = d.F[n], Fy = d.F[N + n], Fz = d.F[2 * N + n];
       const float Qx = d.Q[n], Qy = d.Q[N + n], Qz = d.Q[2 * N + n];
@@ -339,18 +390,6 @@ __global__ void __launch_bounds__(BLK, 3) k_adj_collide(const T *__restrict__ fs
       to_central(k, ux, uy, uz);
       cp27(ks, k);
       collide_cm(ks, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
-      // pull of lambda(t+1): transpose of push with bounce-back
-      Node p = decode(n, kp.nx, kp.ny);
-      float lam[27];
-#pragma unroll
-      for (int q = 0; q < 27; ++q) {
-        if (q == 13) {
-          lam[q] = lam_next[q * N + n];
-          continue;
-        }
-        const int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
-        lam[q] = (mask && mask[m]) ? lam_next[(size_t)(26 - q) * N + n] : lam_next[q * N + m];
-      }
       float gux = 0.0f, guy = 0.0f, guz = 0.0f;
       from_central_vjp(lam, ks, ux, uy, uz, gux, guy, guz);
       float lk[27];
@@ -395,8 +434,9 @@ __global__ void __launch_bounds__(BLK, 3) k_adj_collide(const T *__restrict__ fs
 // a.phi) and the local lmu (into a.mu).
 __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ mask, Fields d, AdjFields a,
                                                     KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N) return;
+  const Site st = site_of(kp);
+  if (!st.in) return;
+  const int n = st.n;
   const size_t N = (size_t)kp.N;
   if (mask && mask[n]) {
     a.rho[n] = 0.0f;
@@ -404,12 +444,11 @@ __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ 
     for (int c = 0; c < 3; ++c) a.u[c * N + n] = a.phi[c * N + n] = 0.0f;
     return;
   }
-  Node p = decode(n, kp.nx, kp.ny);
   float lph[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int q = 0; q < 27; ++q) {
     if (q == 13) continue;
-    const int m = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+    const int m = st.at(-cx_of(q), -cy_of(q), -cz_of(q));
     if (cx_of(q)) lph[0] += cx_of(q) * weight_of(q) * a.Q[m];
     if (cy_of(q)) lph[1] += cy_of(q) * weight_of(q) * a.Q[N + m];
     if (cz_of(q)) lph[2] += cz_of(q) * weight_of(q) * a.Q[2 * N + m];
@@ -456,15 +495,15 @@ __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ 
 
 // lmu(y) = local(y) + 3 sum_q w_q sum_a c_qa lg_a(y - c_q)
 __global__ void __launch_bounds__(256) k_adj_mu(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N) return;
+  const Site st = site_of(kp);
+  if (!st.in) return;
+  const int n = st.n;
   const size_t N = (size_t)kp.N;
-  Node p = decode(n, kp.nx, kp.ny);
   float s = 0.0f;
 #pragma unroll
   for (int q = 0; q < 27; ++q) {
     if (q == 13) continue;
-    const int m = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
+    const int m = st.at(-cx_of(q), -cy_of(q), -cz_of(q));
     float v = 0.0f;
     if (cx_of(q)) v += cx_of(q) * a.phi[m];
     if (cy_of(q)) v += cy_of(q) * a.phi[N + m];
@@ -475,28 +514,25 @@ __global__ void __launch_bounds__(256) k_adj_mu(const uint8_t *__restrict__ mask
 }
 
 // Eq. 36 transposed: mu(b) = sum_q w_q s(b+c_q) mu(b+c_q) / den(b) on solid
-// boundary nodes b.  Gathered at fluid nodes y: sum over solid neighbours
-// b = y - c_q of (w_q / den(b)) lmu(b).
-__device__ __forceinline__ float fluid_weight_sum(const uint8_t *__restrict__ mask, int b, const KParams &kp) {
-  Node p = decode(b, kp.nx, kp.ny);
-  float den = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    if (q == 13) continue;
-    if (!mask[neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp)]) den += weight_of(q);
-  }
-  return den;
-}
-
-__global__ void __launch_bounds__(256) k_adj_wet_mu(const uint8_t *__restrict__ mask, AdjFields a, KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N || mask[n]) return;
-  Node p = decode(n, kp.nx, kp.ny);
+// boundary nodes b.  Gathered at fluid nodes y: sum over the solid
+// neighbours b = y + c_p of (w_p / den(b)) lmu(b), with 1/den(b) stored per
+// node and the solid neighbours read from y's bitmask.
+__global__ void __launch_bounds__(256) k_adj_wet_mu(const uint8_t *__restrict__ mask,
+                                                    const uint32_t *__restrict__ nbr,
+                                                    const float *__restrict__ inv_den, AdjFields a, KParams kp) {
+  const Site st = site_of(kp);
+  if (!st.in) return;
+  const int n = st.n;
+  if (mask[n]) return;
+  const uint32_t solid = nbr[n];
   float add = 0.0f;
-  for (int q = 0; q < 27; ++q) {
-    if (q == 13) continue;
-    const int b = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
-    if (mask[b]) add += weight_of(q) / fluid_weight_sum(mask, b, kp) * a.pm[b];
+  if (solid) {
+#pragma unroll
+    for (int p = 0; p < 27; ++p) {
+      if (p == 13 || !((solid >> p) & 1u)) continue;
+      const int b = st.at(cx_of(p), cy_of(p), cz_of(p));
+      add += weight_of(p) * inv_den[b] * a.pm[b];
+    }
   }
   a.mu[n] = a.pm[n] + add;  // final lmu on fluid nodes into a.mu
 }
@@ -504,24 +540,24 @@ __global__ void __launch_bounds__(256) k_adj_wet_mu(const uint8_t *__restrict__ 
 // mu(x) = mu0(rho(x)) - kappa 6 (sum_q w_q rho(x+c_q) - rho(x)) on fluid x:
 // lrho(y) += [fluid y] (mu0'(rho) + 6 kappa) lmu(y) - 6 kappa sum_q w_q lmu(y+c_q)
 // and dJ/dkappa += -sum_fluid lmu(x) 6 (sum_q w_q rho(x+c_q) - rho(x)).
-__global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mask, Fields d, AdjFields a,
-                                                 const float *__restrict__ lmu, double *__restrict__ partial,
-                                                 KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
+                                                 Fields d, AdjFields a, const float *__restrict__ lmu,
+                                                 double *__restrict__ partial, KParams kp) {
+  const Site st = site_of(kp);
+  const int n = st.n;
   double par[NPAR];
 #pragma unroll
   for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
-  if (n < kp.N) {
+  if (st.in) {
     const bool solid = mask && mask[n];  // lmu: final lmu on fluid nodes; solid entries are not read
-    Node p = decode(n, kp.nx, kp.ny);
+    const uint32_t sn = mask ? nbr[n] : 0u;
     float s = 0.0f, lap = 0.0f;
     const float r = d.rho[n];
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
       if (q == 13) continue;
-      const int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
-      const bool fm = !(mask && mask[m]);
-      if (fm) s += weight_of(q) * lmu[m];
+      const int m = st.at(cx_of(q), cy_of(q), cz_of(q));
+      if (!((sn >> q) & 1u)) s += weight_of(q) * lmu[m];
       lap += weight_of(q) * (d.rho[m] - r);
     }
     float lr;
@@ -543,7 +579,7 @@ __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mas
 // solid density with respect to rho_ave (1, phi, or 0 when clamped) and to the
 // wetting value, and the parameter gradient lrho(b) * d rho_s / d value.
 __global__ void __launch_bounds__(BLK) k_adj_wet_prep(const int *__restrict__ bnd, int nb,
-                                                      const uint8_t *__restrict__ mask, Fields d, AdjFields a,
+                                                      const uint32_t *__restrict__ nbr, Fields d, AdjFields a,
                                                       double *__restrict__ partial, KParams kp) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double par[NPAR];
@@ -551,14 +587,14 @@ __global__ void __launch_bounds__(BLK) k_adj_wet_prep(const int *__restrict__ bn
   for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
   if (t < nb) {
     const int b = bnd[t];
-    Node p = decode(b, kp.nx, kp.ny);
+    const Node p = decode(b, kp.nx, kp.ny);
+    const uint32_t solid = nbr[b];
     float num = 0.0f, den = 0.0f;
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
       if (q == 13) continue;
-      const int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
-      if (!mask[m]) {
-        num += weight_of(q) * d.rho[m];
+      if (!((solid >> q) & 1u)) {
+        num += weight_of(q) * d.rho[neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp)];
         den += weight_of(q);
       }
     }
@@ -586,18 +622,23 @@ __global__ void __launch_bounds__(BLK) k_adj_wet_prep(const int *__restrict__ bn
 // lambda_q(t)(x) = local part + lrho(x) + c_q . lj(x) on fluid nodes, with
 // part 2 of Eqs. 37-38 transposed when there are walls: lrho(y) += sum over
 // solid neighbours b of w_q (dave(b)/den(b)) lrho(b) (stored in a.F).
-__global__ void __launch_bounds__(256) k_adj_out(const uint8_t *__restrict__ mask, int wet, AdjFields a,
-                                                 float *__restrict__ lam_t, KParams kp) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N || (mask && mask[n])) return;
+__global__ void __launch_bounds__(256) k_adj_out(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
+                                                 int wet, AdjFields a, float *__restrict__ lam_t, KParams kp) {
+  const Site st = site_of(kp);
+  if (!st.in) return;
+  const int n = st.n;
+  if (mask && mask[n]) return;
   const size_t N = (size_t)kp.N;
   float lr = a.phi[n];
   if (wet) {
-    Node p = decode(n, kp.nx, kp.ny);
-    for (int q = 0; q < 27; ++q) {
-      if (q == 13) continue;
-      const int b = neighbour(p, -cx_of(q), -cy_of(q), -cz_of(q), kp);
-      if (mask[b]) lr += weight_of(q) * a.F[b];
+    // solid neighbours b = n + c_p (bit p); a.F[b] = dave(b)/den(b) lrho(b)
+    const uint32_t solid = nbr[n];
+    if (solid) {
+#pragma unroll
+      for (int p = 0; p < 27; ++p) {
+        if (p == 13 || !((solid >> p) & 1u)) continue;
+        lr += weight_of(p) * a.F[st.at(cx_of(p), cy_of(p), cz_of(p))];
+      }
     }
   }
   const float jx = a.u[n], jy = a.u[N + n], jz = a.u[2 * N + n];
@@ -785,9 +826,12 @@ struct Regions {
   int gb, gw;
 };
 
+// 3-D launch shape of the node-parallel kernels: 32 x by threads per block
+dim3 grid3(const lbm_ctx *ctx, int by) { return dim3((ctx->nx + 31) / 32, (ctx->ny + by - 1) / by, ctx->nz); }
+
 Regions regions(lbm_ctx *ctx) {
   Regions r;
-  r.gb = (ctx->N + BLK - 1) / BLK;
+  r.gb = (int)adj_blocks(ctx->nx, ctx->ny, ctx->nz);
   r.gw = ctx->n_bnd ? (ctx->n_bnd + BLK - 1) / BLK : 0;
   r.collide = ctx->adj_partial;
   r.rho = ctx->adj_partial + (size_t)r.gb * NPAR;
@@ -800,10 +844,10 @@ Regions regions(lbm_ctx *ctx) {
 void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
-  k_adj_rho<<<R.gb, BLK, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, lmu, R.rho, kp);
+  k_adj_rho<<<grid3(ctx, ADJ_BY), dim3(32, ADJ_BY), 0, s>>>(ctx->mask, ctx->nbr, ctx->fld, ctx->adj, lmu, R.rho, kp);
   ctx->launches++;
   if (ctx->n_bnd) {
-    k_adj_wet_prep<<<R.gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld, ctx->adj, R.wet, kp);
+    k_adj_wet_prep<<<R.gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, ctx->fld, ctx->adj, R.wet, kp);
     ctx->launches++;
   }
 }
@@ -811,11 +855,10 @@ void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R) {
 // lmu: gather of lg (+ the local part), and Eq. 36 transposed with walls
 const float *adj_mu(lbm_ctx *ctx) {
   const KParams &kp = ctx->kp;
-  const int g = (kp.N + 255) / 256;
-  k_adj_mu<<<g, 256, 0, ctx->stream>>>(ctx->mask, ctx->adj, kp);
+  k_adj_mu<<<grid3(ctx, 8), dim3(32, 8), 0, ctx->stream>>>(ctx->mask, ctx->adj, kp);
   ctx->launches++;
   if (!ctx->mask) return ctx->adj.pm;
-  k_adj_wet_mu<<<g, 256, 0, ctx->stream>>>(ctx->mask, ctx->adj, kp);
+  k_adj_wet_mu<<<grid3(ctx, 8), dim3(32, 8), 0, ctx->stream>>>(ctx->mask, ctx->nbr, ctx->inv_den, ctx->adj, kp);
   ctx->launches++;
   return ctx->adj.mu;
 }
@@ -847,7 +890,7 @@ void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam,
   k_obj_seed<<<g, 256, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj, J, kp, rl, rv);
   ctx->launches += 3;
   cudaMemsetAsync(lam, 0, 27 * (size_t)kp.N * sizeof(float), s);
-  k_adj_fields<<<g, 256, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
+  k_adj_fields<<<grid3(ctx, 8), dim3(32, 8), 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
   ctx->launches++;
   const float *lmu = adj_mu(ctx);
   // the objective's direct dependence on kappa and on the wetting value
@@ -857,29 +900,29 @@ void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam,
     k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
     ctx->launches++;
   }
-  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->n_bnd ? 1 : 0, ctx->adj, lam, kp);
+  k_adj_out<<<grid3(ctx, 8), dim3(32, 8), 0, s>>>(ctx->mask, ctx->nbr, ctx->n_bnd ? 1 : 0, ctx->adj, lam, kp);
   ctx->launches++;
 }
 
 void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
-  const int g = (kp.N + 255) / 256;
   const Regions R = regions(ctx);
+  const dim3 g4 = grid3(ctx, ADJ_BY), b4(32, ADJ_BY), g8 = grid3(ctx, 8), b8(32, 8);
   // forward recompute of the fields of f(t) (the state is in ctx->f[cur])
   launch_fields_full(ctx);
   if (ctx->storage == LBM_F16)
-    k_adj_collide<__half><<<R.gb, BLK, 0, s>>>((const __half *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
-                                              ctx->fld, ctx->adj, R.collide, kp);
+    k_adj_collide<__half><<<g4, b4, 0, s>>>((const __half *)f_state, ctx->fld.sb, ctx->mask, ctx->nbr, lam_next,
+                                           lam_t, ctx->fld, ctx->adj, R.collide, kp);
   else
-    k_adj_collide<float><<<R.gb, BLK, 0, s>>>((const float *)f_state, ctx->fld.sb, ctx->mask, lam_next, lam_t,
-                                             ctx->fld, ctx->adj, R.collide, kp);
-  k_adj_fields<<<g, 256, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
+    k_adj_collide<float><<<g4, b4, 0, s>>>((const float *)f_state, ctx->fld.sb, ctx->mask, ctx->nbr, lam_next,
+                                          lam_t, ctx->fld, ctx->adj, R.collide, kp);
+  k_adj_fields<<<g8, b8, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
   ctx->launches += 2;
   const float *lmu = adj_mu(ctx);
   adj_tail(ctx, lmu, R);
   k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
-  k_adj_out<<<g, 256, 0, s>>>(ctx->mask, ctx->n_bnd ? 1 : 0, ctx->adj, lam_t, kp);
+  k_adj_out<<<g8, b8, 0, s>>>(ctx->mask, ctx->nbr, ctx->n_bnd ? 1 : 0, ctx->adj, lam_t, kp);
   ctx->launches += 2;
 }
 

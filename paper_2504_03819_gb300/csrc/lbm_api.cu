@@ -21,12 +21,14 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 //   f[0], f[1]      27 N elements of the storage type each
 //   fields          rho N, j 3N, mu N, u 3N, F 3N, phi 3N, Q 3N, sb 2N floats
 //   boundary list   N ints
+//   neighbours      N uint32 solid-neighbour bitmasks, N floats of inverse
+//                   fluid-weight sums, N/256 + 2 ints of compaction counts
 //   reduction       RED_BLOCKS * 2 doubles
 //   status          2 ints
-//   adjoint         16 N floats, then 3 regions of ceil(N/128)+1 blocks x
+//   adjoint         16 N floats, then 3 regions of adj_blocks() blocks x
 //                   LBM_NGRAD doubles of gradient partials
 struct Layout {
-  size_t f0, f1, fields, bnd, red, status, adj, adj_partial, total;
+  size_t f0, f1, fields, bnd, nbr, inv_den, scan, red, status, adj, adj_partial, total;
 };
 
 bool layout(int nx, int ny, int nz, int storage, Layout *L) {
@@ -40,10 +42,13 @@ bool layout(int nx, int ny, int nz, int storage, Layout *L) {
   L->f1 = off; off = align_up(off + 27 * (size_t)N * elem);
   L->fields = off; off = align_up(off + 19 * (size_t)N * sizeof(float));
   L->bnd = off; off = align_up(off + (size_t)N * sizeof(int));
+  L->nbr = off; off = align_up(off + (size_t)N * sizeof(uint32_t));
+  L->inv_den = off; off = align_up(off + (size_t)N * sizeof(float));
+  L->scan = off; off = align_up(off + (size_t)(N / 256 + 2) * sizeof(int));
   L->red = off; off = align_up(off + (size_t)RED_BLOCKS * 2 * sizeof(double));
   L->status = off; off = align_up(off + 2 * sizeof(int));
   L->adj = off; off = align_up(off + 16 * (size_t)N * sizeof(float));
-  L->adj_partial = off; off = align_up(off + 3 * (size_t)((N + 127) / 128 + 1) * LBM_NGRAD * sizeof(double));
+  L->adj_partial = off; off = align_up(off + 3 * adj_blocks(nx, ny, nz) * LBM_NGRAD * sizeof(double));
   L->total = off;
   return true;
 }
@@ -152,6 +157,9 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
   ctx->fld.Q = fl + 14 * N;
   ctx->fld.sb = fl + 17 * N;
   ctx->bnd = (int *)(base + L.bnd);
+  ctx->nbr = (uint32_t *)(base + L.nbr);
+  ctx->inv_den = (float *)(base + L.inv_den);
+  ctx->scan = (int *)(base + L.scan);
   ctx->red_partial = (double *)(base + L.red);
   ctx->status = (int *)(base + L.status);
   float *ad = (float *)(base + L.adj);
@@ -235,6 +243,7 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
     k.ref_dmu[i] = (float)(mu0((double)(float)refs[i]) - mu_ref);
     k.ref_inv[i] = (float)(1.0 / (double)(float)refs[i]);
     k.ref_bomb[i] = (float)(p->b / (1.0 - p->b * (double)(float)refs[i]));
+    k.ref_bomb2[i] = (float)(p->b / ((1.0 - p->b * (double)(float)refs[i]) * (1.0 - p->b * (double)(float)refs[i])));
   }
   ctx->have_params = 1;
   return LBM_OK;

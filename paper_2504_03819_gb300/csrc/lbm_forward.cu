@@ -66,16 +66,21 @@ __global__ void __launch_bounds__(BLOCK) k_moments(const T *__restrict__ f, cons
 // ---------------------------------------------------------------------------
 // wetting boundary (Eqs. 36-38) on the listed solid nodes
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float fluid_average(const float *__restrict__ g, const uint8_t *__restrict__ mask,
-                                               int n, const KParams &kp) {
-  Node p = decode(n, kp.nx, kp.ny);
+// weighted mean of g over the fluid neighbours of solid node n; `solid` has
+// bit q set when n + c_q is solid
+__device__ __forceinline__ float fluid_average(const float *__restrict__ g, uint32_t solid, int n,
+                                               const KParams &kp) {
+  const Node p = decode(n, kp.nx, kp.ny);
+  const int ox[3] = {p.x == 0 ? kp.nx - 1 : -1, 0, p.x == kp.nx - 1 ? -(kp.nx - 1) : 1};
+  const int oy[3] = {p.y == 0 ? (kp.ny - 1) * kp.nx : -kp.nx, 0, p.y == kp.ny - 1 ? -(kp.ny - 1) * kp.nx : kp.nx};
+  const int nxy = kp.nx * kp.ny;
+  const int oz[3] = {p.z == 0 ? (kp.nz - 1) * nxy : -nxy, 0, p.z == kp.nz - 1 ? -(kp.nz - 1) * nxy : nxy};
   float num = 0.0f, den = 0.0f;
 #pragma unroll
   for (int q = 0; q < 27; ++q) {
     if (q == 13) continue;
-    int m = neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp);
-    if (!mask[m]) {
-      num += weight_of(q) * g[m];
+    if (!((solid >> q) & 1u)) {
+      num += weight_of(q) * g[n + ox[cx_of(q) + 1] + oy[cy_of(q) + 1] + oz[cz_of(q) + 1]];
       den += weight_of(q);
     }
   }
@@ -83,11 +88,11 @@ __device__ __forceinline__ float fluid_average(const float *__restrict__ g, cons
 }
 
 __global__ void __launch_bounds__(BLOCK) k_wet_rho(const int *__restrict__ bnd, int nb,
-                                                   const uint8_t *__restrict__ mask, float *rho, KParams kp) {
+                                                   const uint32_t *__restrict__ nbr, float *rho, KParams kp) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nb) return;
   int n = bnd[t];
-  float ave = fluid_average(rho, mask, n, kp);
+  float ave = fluid_average(rho, nbr[n], n, kp);
   float rs = ave;
   if (kp.wet_mode != LBM_WET_NEUTRAL && ave >= kp.band_lo && ave <= kp.band_hi) {
     float m = kp.wet_mode == LBM_WET_PHI ? kp.wet_value * ave : ave - kp.wet_value;
@@ -97,11 +102,11 @@ __global__ void __launch_bounds__(BLOCK) k_wet_rho(const int *__restrict__ bnd, 
 }
 
 __global__ void __launch_bounds__(BLOCK) k_wet_mu(const int *__restrict__ bnd, int nb,
-                                                  const uint8_t *__restrict__ mask, float *mu, KParams kp) {
+                                                  const uint32_t *__restrict__ nbr, float *mu, KParams kp) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nb) return;
   int n = bnd[t];
-  mu[n] = fluid_average(mu, mask, n, kp);
+  mu[n] = fluid_average(mu, nbr[n], n, kp);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,17 +248,74 @@ __global__ void __launch_bounds__(BLOCK) k_init_f(const float *__restrict__ rho,
 // ---------------------------------------------------------------------------
 // boundary list, population copies, FP64 reductions
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BLOCK) k_mark_boundary(const uint8_t *__restrict__ mask, int *__restrict__ bnd,
-                                                         int *__restrict__ counter, KParams kp) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= kp.N || !mask[n]) return;
-  Node p = decode(n, kp.nx, kp.ny);
-  bool any = false;
-  for (int q = 0; q < 27; ++q) {
-    if (q == 13) continue;
-    if (!mask[neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp)]) any = true;
+// Boundary bookkeeping of a domain with walls, computed once: per node the
+// solid-neighbour bitmask and, for solid nodes with fluid neighbours, the
+// inverse fluid-weight sum of Eqs. 36-37 and a per-block count; then the
+// list of those nodes in node order (a deterministic compaction).
+__global__ void __launch_bounds__(BLOCK) k_mark_nbr(const uint8_t *__restrict__ mask, uint32_t *__restrict__ nbr,
+                                                    float *__restrict__ inv_den, int *__restrict__ counts,
+                                                    KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  bool boundary = false;
+  if (n < kp.N) {
+    const Node p = decode(n, kp.nx, kp.ny);
+    uint32_t bits = 0;
+    float den = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      if (q == 13) continue;
+      if (mask[neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp)])
+        bits |= 1u << q;
+      else
+        den += weight_of(q);
+    }
+    nbr[n] = bits;
+    boundary = mask[n] && den > 0.0f;
+    inv_den[n] = boundary ? 1.0f / den : 0.0f;
   }
-  if (any) bnd[atomicAdd(counter, 1)] = n;
+  const int c = __syncthreads_count(boundary);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// exclusive prefix sum of the per-block counts in place (one block of
+// SCAN_T threads, each a contiguous chunk); the total goes to *total
+constexpr int SCAN_T = 1024;
+__global__ void __launch_bounds__(SCAN_T) k_scan_counts(int *__restrict__ counts, int nblocks, int *__restrict__ total) {
+  __shared__ int part[SCAN_T];
+  const int t = threadIdx.x;
+  const int chunk = (nblocks + SCAN_T - 1) / SCAN_T;
+  const int b0 = min(t * chunk, nblocks), b1 = min(b0 + chunk, nblocks);
+  int sum = 0;
+  for (int b = b0; b < b1; ++b) sum += counts[b];
+  part[t] = sum;
+  __syncthreads();
+  for (int w = 1; w < SCAN_T; w <<= 1) {  // inclusive scan of the chunk sums
+    const int v = t >= w ? part[t - w] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - sum;
+  for (int b = b0; b < b1; ++b) {
+    const int c = counts[b];
+    counts[b] = run;
+    run += c;
+  }
+  if (t == SCAN_T - 1) *total = part[t];
+}
+
+__global__ void __launch_bounds__(BLOCK) k_write_bnd(const float *__restrict__ inv_den, const int *__restrict__ offsets,
+                                                     int *__restrict__ bnd, KParams kp) {
+  __shared__ int warp_base[BLOCK / 32];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool boundary = n < kp.N && inv_den[n] > 0.0f;
+  const unsigned ball = __ballot_sync(0xffffffffu, boundary);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_base[w] = __popc(ball);
+  __syncthreads();
+  int base = offsets[blockIdx.x];
+  for (int i = 0; i < w; ++i) base += warp_base[i];
+  if (boundary) bnd[base + __popc(ball & ((1u << lane) - 1u))] = n;
 }
 
 template <typename T>
@@ -358,10 +420,10 @@ void fields_impl(lbm_ctx *ctx, bool with_u) {
   cudaStream_t s = ctx->stream;
   k_moments<T><<<g, BLOCK, 0, s>>>(fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
   ctx->launches++;
-  if (ctx->n_bnd) { k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.rho, kp); ctx->launches++; }
+  if (ctx->n_bnd) { k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, d.rho, kp); ctx->launches++; }
   k_mu<<<g, BLOCK, 0, s>>>(d.rho, ctx->mask, d.mu, kp);
   ctx->launches++;
-  if (ctx->n_bnd) { k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.mu, kp); ctx->launches++; }
+  if (ctx->n_bnd) { k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, d.mu, kp); ctx->launches++; }
   if (with_u) {
     k_uphi<<<g, BLOCK, 0, s>>>(d.rho, d.j, d.mu, ctx->mask, d.u, d.F, d.phi, kp);
     ctx->launches++;
@@ -371,8 +433,11 @@ void fields_impl(lbm_ctx *ctx, bool with_u) {
 }  // namespace
 
 void launch_mark_boundary(lbm_ctx *ctx) {
-  k_mark_boundary<<<blocks_for(ctx->N), BLOCK, 0, ctx->stream>>>(ctx->mask, ctx->bnd, ctx->status + 1, ctx->kp);
-  ctx->launches++;
+  const int g = blocks_for(ctx->N);
+  k_mark_nbr<<<g, BLOCK, 0, ctx->stream>>>(ctx->mask, ctx->nbr, ctx->inv_den, ctx->scan, ctx->kp);
+  k_scan_counts<<<1, SCAN_T, 0, ctx->stream>>>(ctx->scan, g, ctx->status + 1);
+  k_write_bnd<<<g, BLOCK, 0, ctx->stream>>>(ctx->inv_den, ctx->scan, ctx->bnd, ctx->kp);
+  ctx->launches += 3;
 }
 
 void launch_step(lbm_ctx *ctx) { launch_step_fused(ctx); }
@@ -388,12 +453,12 @@ void launch_fields_full(lbm_ctx *ctx) {
 
 void launch_wet_rho(lbm_ctx *ctx) {
   TimedLaunch t(ctx, K_WET_RHO);
-  k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld.rho, ctx->kp);
+  k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, ctx->fld.rho, ctx->kp);
 }
 
 void launch_wet_mu(lbm_ctx *ctx) {
   TimedLaunch t(ctx, K_WET_MU);
-  k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->mask, ctx->fld.mu, ctx->kp);
+  k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, ctx->fld.mu, ctx->kp);
 }
 
 void launch_fields(lbm_ctx *ctx, bool with_u) {
@@ -410,10 +475,10 @@ void launch_init(lbm_ctx *ctx, const float *rho0, const float *u0) {
   cudaStream_t s = ctx->stream;
   k_init_rho<<<g, BLOCK, 0, s>>>(rho0, ctx->mask, d.rho, kp);
   ctx->launches++;
-  if (ctx->n_bnd) { k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.rho, kp); ctx->launches++; }
+  if (ctx->n_bnd) { k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, d.rho, kp); ctx->launches++; }
   k_mu<<<g, BLOCK, 0, s>>>(d.rho, ctx->mask, d.mu, kp);
   ctx->launches++;
-  if (ctx->n_bnd) { k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->mask, d.mu, kp); ctx->launches++; }
+  if (ctx->n_bnd) { k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, d.mu, kp); ctx->launches++; }
   if (ctx->storage == LBM_F16)
     k_init_f<__half><<<g, BLOCK, 0, s>>>(d.rho, d.mu, u0, ctx->mask, (__half *)ctx->f[ctx->cur], d.sb, kp);
   else

@@ -31,6 +31,7 @@ struct KParams {
   float rho_split;
   float ref_rho[2], ref_omb[2], ref_dmu[2];  // [0] vapour, [1] liquid: rho_r, 1 - b rho_r, mu0(rho_r) - mu_ref
   float ref_inv[2], ref_bomb[2];             // 1 / rho_r, b / (1 - b rho_r)
+  float ref_bomb2[2];                        // b / (1 - b rho_r)^2
 };
 
 // Device views carved out of the caller's workspace.
@@ -83,7 +84,10 @@ struct lbm_ctx {
   cudaStream_t stream;
   const uint8_t *mask;  // device, may be null
   int n_bnd;
-  int *bnd;             // solid nodes with at least one fluid neighbour
+  int *bnd;             // solid nodes with at least one fluid neighbour, in node order
+  uint32_t *nbr;        // per node: bit q set when node + c_q is solid (walls only)
+  float *inv_den;       // per solid boundary node: 1 / sum of w_q over fluid neighbours, else 0
+  int *scan;            // per-block counts of the boundary-list compaction
   void *f[2];
   int cur;
   lbm::Fields fld;
@@ -108,6 +112,13 @@ struct lbm_ctx {
 namespace lbm {
 
 constexpr int RED_BLOCKS = 1024;
+
+// Node-parallel adjoint kernels run on 3-D grids of 32 x ADJ_BY x 1 blocks
+// (x fastest); the number of blocks sizes their per-block partial sums.
+constexpr int ADJ_BY = 4;
+inline size_t adj_blocks(int nx, int ny, int nz) {
+  return (size_t)((nx + 31) / 32) * (size_t)((ny + ADJ_BY - 1) / ADJ_BY) * (size_t)nz;
+}
 constexpr int STATUS_NONFINITE = 1;
 constexpr int STATUS_DOMAIN = 2;
 constexpr int STATUS_TIMEOUT = 4;

@@ -217,12 +217,17 @@ __device__ __forceinline__ void collide_cm(float k[27], float pm, float Fx, floa
 //   ln((1 + A)/(1 - C)) = log1p((A + C)/(1 - C)),
 // holds exactly; every term is O(d), so FP32 keeps its relative precision
 // where the direct form cancels (liquid: RT(...) ~ 2.5 against 2 a rho ~ 2.3).
+// Both quotients share 1/(1 - C): 1 - b rho = (1 - b rho_r)(1 - C), so
+// C/(1 - b rho) = d b/(1 - b rho_r)^2 / (1 - C); one correctly rounded
+// reciprocal replaces the two divisions.
 __device__ __forceinline__ float mu0_vdw(float r, const KParams &kp) {
-  const int ph = r > kp.rho_split ? 1 : 0;
-  const float d = r - kp.ref_rho[ph];
-  const float A = d * kp.ref_inv[ph], Cc = d * kp.ref_bomb[ph];
-  const float t = log1pf((A + Cc) / (1.0f - Cc)) + Cc / (1.0f - kp.b * r);
-  return kp.ref_dmu[ph] + kp.RT * t - 2.0f * kp.a * d;
+  const bool liq = r > kp.rho_split;
+  const float d = r - (liq ? kp.ref_rho[1] : kp.ref_rho[0]);
+  const float A = d * (liq ? kp.ref_inv[1] : kp.ref_inv[0]);
+  const float Cc = d * (liq ? kp.ref_bomb[1] : kp.ref_bomb[0]);
+  const float rc = __frcp_rn(1.0f - Cc);
+  const float t = log1pf((A + Cc) * rc) + d * (liq ? kp.ref_bomb2[1] : kp.ref_bomb2[0]) * rc;
+  return (liq ? kp.ref_dmu[1] : kp.ref_dmu[0]) + kp.RT * t - 2.0f * kp.a * d;
 }
 
 // p_m = (1 + mu)/3 from mu' = mu - mu_ref.

@@ -10,11 +10,16 @@ namespace {
 
 // Scratch layout for N <= LBM_NOALLOC_MAX_NODES nodes, mirroring the field
 // part of the workspace: 19 floats per node (rho, j, mu', u, F, phi, Q, shift
-// bases), the boundary list (one int per node) and two status ints.
+// bases), the boundary list (one int per node), the solid-neighbour bitmasks
+// and inverse fluid-weight sums (one word each per node), the compaction
+// counts (one int per 256 nodes) and two status ints.
 constexpr size_t kMax = LBM_NOALLOC_MAX_NODES;
 constexpr size_t kFieldBytes = 19 * kMax * sizeof(float);
-constexpr size_t kBndBytes = kMax * sizeof(int);
-constexpr size_t kStatusOff = kFieldBytes + kBndBytes;
+constexpr size_t kBndOff = kFieldBytes;
+constexpr size_t kNbrOff = kBndOff + kMax * sizeof(int);
+constexpr size_t kInvDenOff = kNbrOff + kMax * sizeof(uint32_t);
+constexpr size_t kScanOff = kInvDenOff + kMax * sizeof(float);
+constexpr size_t kStatusOff = kScanOff + (kMax / 256 + 2) * sizeof(int);
 constexpr size_t kScratchBytes = kStatusOff + 256;
 
 // Every GPU that loads the library holds this array until the process exits.
@@ -75,7 +80,10 @@ extern "C" int lbm_step_noalloc(const float *f_in, float *f_out, const uint8_t *
   ctx.fld.phi = fl + 11 * n;
   ctx.fld.Q = fl + 14 * n;
   ctx.fld.sb = fl + 17 * n;
-  ctx.bnd = (int *)((char *)base + kFieldBytes);
+  ctx.bnd = (int *)((char *)base + kBndOff);
+  ctx.nbr = (uint32_t *)((char *)base + kNbrOff);
+  ctx.inv_den = (float *)((char *)base + kInvDenOff);
+  ctx.scan = (int *)((char *)base + kScanOff);
   ctx.red_partial = nullptr;
   ctx.status = (int *)((char *)base + kStatusOff);
   ctx.kp.nx = nx;

@@ -72,12 +72,25 @@ __global__ void __launch_bounds__(256) k_moments_v(const T *__restrict__ f, cons
 // chemical potential, z-marching (Eqs. 2, 32)
 // ---------------------------------------------------------------------------
 constexpr int MX = 32, MY = 8;   // tile of k_mu_z
+constexpr int MU_DEPTH = 4;      // rho planes in flight ahead of the stencil
 
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
+// Each block marches a 32 x 8 column through z.  The rho planes (with a
+// one-node periodic ring) stream into a shared-memory ring by asynchronous
+// copies issued MU_DEPTH planes ahead, so several planes per block are in
+// flight while the stencil works on planes z-1, z, z+1.
 __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, const uint8_t *__restrict__ mask,
                                                  float *__restrict__ mu, KParams kp, int MZ) {
   constexpr int HX = MX + 2, HY = MY + 2, HP = HX * HY;
-  __shared__ float s_r[3][HP];
+  constexpr int NR = MU_DEPTH + 3;  // planes z-1 .. z+1 being read, MU_DEPTH in flight, one being refilled
+  __shared__ float s_r[NR][HP];
   const int tx = threadIdx.x % MX, ty = threadIdx.x / MX;
   const int x0 = blockIdx.x * MX, y0 = blockIdx.y * MY, z0 = blockIdx.z * MZ;
   const int z1 = min(z0 + MZ, kp.nz);
@@ -91,34 +104,27 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
     const int hx = k % HX, hy = k / HX;
     slot_xy[s] = k < HP ? pmod(x0 + hx - 1, kp.nx) + kp.nx * pmod(y0 + hy - 1, kp.ny) : 0;
   }
-  // the next plane is fetched into registers one iteration ahead
-  float pre[SLOTS];
-  auto fetch_plane = [&](int z) {
-    const size_t zoff = (size_t)nxy * pmod(z, kp.nz);
+  auto ring = [&](int z) { return (z - z0 + 1 + NR) % NR; };  // z >= z0 - 1
+  // asynchronous copy of plane z into its ring slot (one commit group per
+  // plane, empty past the end of the column)
+  auto issue = [&](int z, int slot) {
+    if (z <= z1) {
+      const float *src = rho + (size_t)nxy * pmod(z, kp.nz);
+      float *dst = s_r[slot];
 #pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      const int k = threadIdx.x + s * MX * MY;
-      pre[s] = k < HP ? __ldg(rho + zoff + slot_xy[s]) : 0.0f;
+      for (int s = 0; s < SLOTS; ++s) {
+        const int k = threadIdx.x + s * MX * MY;
+        if (k < HP) cp_async4(dst + k, src + slot_xy[s]);
+      }
     }
-  };
-  auto store_plane = [&](int z) {
-    const int ring = (z + 3 * kp.nz + 3) % 3;
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      const int k = threadIdx.x + s * MX * MY;
-      if (k < HP) s_r[ring][k] = pre[s];
-    }
-  };
-  auto load_plane = [&](int z) {
-    fetch_plane(z);
-    store_plane(z);
+    cp_async_commit();
   };
   const int x = x0 + tx, y = y0 + ty;
   const bool inside = x < kp.nx && y < kp.ny;
   // D(z') = sum_{cx,cy} w1 w1 (rho(x+cx, y+cy, z') - rho(x, y, z')) about
   // each plane's own centre: small numbers, accurate in FP32
-  auto plane_sum = [&](int z, float &centre) {
-    const float *p = s_r[(z + 3 * kp.nz + 3) % 3];
+  auto plane_sum = [&](int slot, float &centre) {
+    const float *p = s_r[slot];
     const int c = (ty + 1) * HX + tx + 1;
     centre = p[c];
     const float row_m = w1(1) * (p[c - HX - 1] - centre) + w1(0) * (p[c - HX] - centre) + w1(1) * (p[c - HX + 1] - centre);
@@ -126,19 +132,23 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
     const float row_p = w1(1) * (p[c + HX - 1] - centre) + w1(0) * (p[c + HX] - centre) + w1(1) * (p[c + HX + 1] - centre);
     return w1(1) * row_m + w1(0) * row_0 + w1(1) * row_p;
   };
-  load_plane(z0 - 1);
-  load_plane(z0);
-  fetch_plane(z0 + 1);
+  // prologue: planes z0-1 .. z0+MU_DEPTH in flight, the first three waited for
+  for (int z = z0 - 1; z <= z0 + MU_DEPTH; ++z) issue(z, ring(z));
+  cp_async_wait<MU_DEPTH - 1>();
   __syncthreads();
   float dm, cm, d0, c0, dp, cp;
-  dm = plane_sum(z0 - 1, cm);
-  d0 = plane_sum(z0, c0);
+  dm = plane_sum(ring(z0 - 1), cm);
+  d0 = plane_sum(ring(z0), c0);
+  int slot_in = ring(z0 + MU_DEPTH + 1), slot_next = ring(z0 + 1);  // rotate with z
+  auto advance = [](int s) { return s + 1 == NR ? 0 : s + 1; };
   for (int z = z0; z < z1; ++z) {
-    __syncthreads();  // the slot of plane z - 2 is free
-    store_plane(z + 1);
-    if (z + 1 < z1) fetch_plane(z + 2);
+    // plane z+1 has landed for every thread; the slot of plane z-2 is free
+    cp_async_wait<MU_DEPTH - 1>();
     __syncthreads();
-    dp = plane_sum(z + 1, cp);
+    issue(z + MU_DEPTH + 1, slot_in);
+    dp = plane_sum(slot_next, cp);
+    slot_in = advance(slot_in);
+    slot_next = advance(slot_next);
     if (inside) {
       const int n = x + kp.nx * y + nxy * z;
       if (!(mask && mask[n])) {
@@ -152,20 +162,22 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
     d0 = dp;
     c0 = cp;
   }
+  cp_async_wait<0>();  // no copy outlives the block
 }
 
 // ---------------------------------------------------------------------------
 // fused force / correction / collision / streaming
 // ---------------------------------------------------------------------------
 // column tile: one thread per (x, y); FUSED_MINB blocks per SM are requested
+// (32 x 4 with three blocks per SM measured fastest on GB300)
 #ifndef LBM_FUSED_TX
 #define LBM_FUSED_TX 32
 #endif
 #ifndef LBM_FUSED_TY
-#define LBM_FUSED_TY 8
+#define LBM_FUSED_TY 4
 #endif
 #ifndef LBM_FUSED_MINB
-#define LBM_FUSED_MINB 2
+#define LBM_FUSED_MINB 3
 #endif
 constexpr int TX = LBM_FUSED_TX, TY = LBM_FUSED_TY;
 constexpr int NT = TX * TY;

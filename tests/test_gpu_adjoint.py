@@ -167,3 +167,26 @@ def test_autograd_function_backward():
     assert float(J) == pytest.approx(ref["J"], rel=1e-5)
     assert float(theta.grad[12]) == pytest.approx(ref["wetting_value"], rel=1e-3)
     assert relmax(r0.grad, ref["rho0"]) < 1e-3
+
+
+def test_adjoint_step_bitwise_deterministic():
+    """Two domains built independently (their own boundary lists) give the
+    same lambda(t) and parameter gradient bit for bit: every reduction of the
+    adjoint runs in a fixed order."""
+    case = build("wall_tiles")
+    fr = perturbed(case, oracle_init(case), seed=51)
+    nx, ny, nz = case["n"]
+    g = torch.Generator().manual_seed(8)
+    lam = (torch.randn(27, nz, ny, nx, generator=g, dtype=DT)
+           * torch.from_numpy(~case["mask"].astype(bool)).to(DT)).float().cuda()
+    out = []
+    for _ in range(2):
+        d = gpu(case)
+        d.set_populations(fr.float())
+        raw = d.get_state().clone()
+        grad = torch.zeros(Bd.NGRAD, dtype=DT, device="cuda")
+        lt = d.adjoint_step(raw, lam, grad)
+        out.append((lt.clone(), grad.clone()))
+        d.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
