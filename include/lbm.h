@@ -248,15 +248,25 @@ int lbm_adjoint_init(lbm_ctx *ctx, const float *rho0, const float *u0, const flo
                      double *grad_params, float *grad_rho0);
 
 /*
+ * Bytes per step of the pool of lbm_adjoint_segment: one raw state
+ * (lbm_state_bytes) plus the fields the recompute captures for the adjoint
+ * (rho, mu, u, F, Q: 11*N floats), 256-byte aligned.  0 before
+ * lbm_set_params.
+ */
+size_t lbm_adjoint_pool_bytes(const lbm_ctx *ctx);
+
+/*
  * Adjoint sweep over one checkpoint segment of n >= 1 steps, enqueued from
  * the library (no per-step host round trip).  ckpt: raw state at t0
  * (device, lbm_state_bytes bytes); state_pool: device buffer of
- * n * lbm_state_bytes bytes that receives the recomputed states t0 ..
- * t0+n-1 (the step writes into it directly); lam: device, 27*N floats, on
- * entry dJ/df(t0+n), on return dJ/df(t0); lam_tmp: device, 27*N floats of
- * scratch; grad_params: accumulated as in lbm_adjoint_step.  The context's
- * current state becomes ckpt.  Equivalent to n calls of lbm_adjoint_step on
- * the recomputed states.
+ * n * lbm_adjoint_pool_bytes bytes that receives the recomputed states t0 ..
+ * t0+n-1 and, for t0 .. t0+n-2, the fields the fused step computed from them
+ * (the step writes into it directly, so the adjoint does not recompute
+ * them); lam: device, 27*N floats, on entry dJ/df(t0+n), on return
+ * dJ/df(t0); lam_tmp: device, 27*N floats of scratch; grad_params:
+ * accumulated as in lbm_adjoint_step.  The context's current state becomes
+ * ckpt.  Equivalent to n calls of lbm_adjoint_step on the recomputed states
+ * (up to FP32 rounding of the fields).
  */
 int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool, float *lam, float *lam_tmp,
                         double *grad_params);

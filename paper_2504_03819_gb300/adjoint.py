@@ -46,7 +46,7 @@ def backward_from(dom: Domain, ckpts: dict, nsteps: int, lam, grad, rho0, u0):
     """Adjoint sweep from dJ/df(T) = lam back to dJ/drho0: one
     lbm_adjoint_segment per checkpoint segment, last to first."""
     seg = max(b - a for a, b in zip(sorted(ckpts), sorted(ckpts)[1:] + [nsteps]))
-    pool = torch.empty(seg * dom.state_bytes(), dtype=torch.uint8, device=dom.device)
+    pool = torch.empty(seg * dom.adjoint_pool_bytes(), dtype=torch.uint8, device=dom.device)
     lam_a, lam_b = lam.clone(), torch.empty_like(lam)
     t_end = nsteps
     for s0 in sorted(ckpts, reverse=True):

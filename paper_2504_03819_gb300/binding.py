@@ -42,6 +42,7 @@ SIGNATURES = {
     "lbm_set_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_objective": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_adjoint_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_adjoint_pool_bytes": (C.c_size_t, [C.c_void_p]),
     "lbm_adjoint_segment": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
     "lbm_adjoint_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -300,10 +301,15 @@ class Domain:
                     "lbm_adjoint_step")
         return out
 
+    def adjoint_pool_bytes(self) -> int:
+        """Bytes per step of the adjoint_segment pool (raw state + captured fields)."""
+        return int(self.lib.lbm_adjoint_pool_bytes(self.ctx))
+
     def adjoint_segment(self, ckpt, n: int, pool, lam, lam_tmp, grad):
         """In place: lam = dJ/df(t0+n) -> dJ/df(t0) over the n steps after the
-        raw checkpoint ckpt; pool holds >= n raw states (uint8, CUDA)."""
-        assert pool.numel() >= n * self.state_bytes() and grad.numel() == NGRAD
+        raw checkpoint ckpt; pool holds >= n * adjoint_pool_bytes() bytes
+        (uint8, CUDA)."""
+        assert pool.numel() >= n * self.adjoint_pool_bytes() and grad.numel() == NGRAD
         self._check(self.lib.lbm_adjoint_segment(self.ctx, _ptr(ckpt), int(n), _ptr(pool), _ptr(lam),
                                                  _ptr(lam_tmp), _ptr(grad)), "lbm_adjoint_segment")
         return lam

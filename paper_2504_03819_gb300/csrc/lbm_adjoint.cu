@@ -841,13 +841,13 @@ Regions regions(lbm_ctx *ctx) {
 
 // mu -> rho transpose, wetting part 1, and the output kernel shared by the
 // three entry points; lmu is the final adjoint of mu on fluid nodes
-void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R) {
+void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R, const Fields &d) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
-  k_adj_rho<<<grid3(ctx, ADJ_BY), dim3(32, ADJ_BY), 0, s>>>(ctx->mask, ctx->nbr, ctx->fld, ctx->adj, lmu, R.rho, kp);
+  k_adj_rho<<<grid3(ctx, ADJ_BY), dim3(32, ADJ_BY), 0, s>>>(ctx->mask, ctx->nbr, d, ctx->adj, lmu, R.rho, kp);
   ctx->launches++;
   if (ctx->n_bnd) {
-    k_adj_wet_prep<<<R.gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, ctx->fld, ctx->adj, R.wet, kp);
+    k_adj_wet_prep<<<R.gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, d, ctx->adj, R.wet, kp);
     ctx->launches++;
   }
 }
@@ -872,7 +872,7 @@ void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, doubl
   k_adj_init<<<g, 256, 0, s>>>(ctx->mask, u0, lam0, ctx->fld, ctx->adj, kp);
   ctx->launches++;
   cudaMemsetAsync(R.collide, 0, (size_t)R.gb * NPAR * sizeof(double), s);
-  adj_tail(ctx, ctx->adj.mu, R);
+  adj_tail(ctx, ctx->adj.mu, R, ctx->fld);
   k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
   k_adj_grad_rho0<<<g, 256, 0, s>>>(ctx->mask, ctx->n_bnd ? 1 : 0, ctx->adj, grad_rho0, kp);
   ctx->launches += 2;
@@ -895,7 +895,7 @@ void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam,
   const float *lmu = adj_mu(ctx);
   // the objective's direct dependence on kappa and on the wetting value
   cudaMemsetAsync(R.collide, 0, (size_t)R.gb * NPAR * sizeof(double), s);
-  adj_tail(ctx, lmu, R);
+  adj_tail(ctx, lmu, R, ctx->fld);
   if (grad) {
     k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
     ctx->launches++;
@@ -904,23 +904,35 @@ void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam,
   ctx->launches++;
 }
 
-void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad) {
+void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad,
+                         const float *captured, const float *sb_state) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
   const Regions R = regions(ctx);
   const dim3 g4 = grid3(ctx, ADJ_BY), b4(32, ADJ_BY), g8 = grid3(ctx, 8), b8(32, 8);
-  // forward recompute of the fields of f(t) (the state is in ctx->f[cur])
-  launch_fields_full(ctx);
+  Fields d = ctx->fld;
+  const float *sb = ctx->fld.sb;
+  if (captured) {  // fields of f(t) from the recompute: rho, mu', u, F, Q
+    const size_t N = (size_t)kp.N;
+    d.rho = const_cast<float *>(captured);
+    d.mu = d.rho + N;
+    d.u = d.rho + 2 * N;
+    d.F = d.rho + 5 * N;
+    d.Q = d.rho + 8 * N;
+    sb = sb_state;
+  } else {
+    launch_fields_full(ctx);  // forward recompute of the fields of f(t) (the state is in ctx->f[cur])
+  }
   if (ctx->storage == LBM_F16)
-    k_adj_collide<__half><<<g4, b4, 0, s>>>((const __half *)f_state, ctx->fld.sb, ctx->mask, ctx->nbr, lam_next,
-                                           lam_t, ctx->fld, ctx->adj, R.collide, kp);
+    k_adj_collide<__half><<<g4, b4, 0, s>>>((const __half *)f_state, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d,
+                                           ctx->adj, R.collide, kp);
   else
-    k_adj_collide<float><<<g4, b4, 0, s>>>((const float *)f_state, ctx->fld.sb, ctx->mask, ctx->nbr, lam_next,
-                                          lam_t, ctx->fld, ctx->adj, R.collide, kp);
-  k_adj_fields<<<g8, b8, 0, s>>>(ctx->mask, ctx->fld, ctx->adj, kp);
+    k_adj_collide<float><<<g4, b4, 0, s>>>((const float *)f_state, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d,
+                                          ctx->adj, R.collide, kp);
+  k_adj_fields<<<g8, b8, 0, s>>>(ctx->mask, d, ctx->adj, kp);
   ctx->launches += 2;
   const float *lmu = adj_mu(ctx);
-  adj_tail(ctx, lmu, R);
+  adj_tail(ctx, lmu, R, d);
   k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
   k_adj_out<<<g8, b8, 0, s>>>(ctx->mask, ctx->nbr, ctx->n_bnd ? 1 : 0, ctx->adj, lam_t, kp);
   ctx->launches += 2;

@@ -370,6 +370,11 @@ int lbm_adjoint_step(lbm_ctx *ctx, const void *state_t, const float *lam_next, f
   return check_cuda(ctx, "lbm_adjoint_step");
 }
 
+size_t lbm_adjoint_pool_bytes(const lbm_ctx *ctx) {
+  if (!ctx || !ctx->have_params) return 0;
+  return align_up(align_up(lbm_state_bytes(ctx)) + 11 * (size_t)ctx->N * sizeof(float));
+}
+
 int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool, float *lam, float *lam_tmp,
                         double *grad_params) {
   if (!ctx || !ckpt || n < 1 || !state_pool || !lam || !lam_tmp || !grad_params || lam == lam_tmp)
@@ -378,28 +383,38 @@ int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool,
   const size_t pops = 27 * (size_t)ctx->N * (ctx->storage == LBM_F16 ? 2 : 4);
   const bool rest = ctx->kp.shift_mode == LBM_SHIFT_REST;
   const size_t sbb = rest ? 2 * (size_t)ctx->N * sizeof(float) : 0, sbytes = pops + sbb;
+  const size_t stride = lbm_adjoint_pool_bytes(ctx), cap_off = align_up(sbytes);
   char *pool = (char *)state_pool;
+  auto slot = [&](int i) { return pool + (size_t)i * stride; };
   cudaStream_t s = ctx->stream;
   cudaGetLastError();
   cudaMemcpyAsync(pool, ckpt, sbytes, cudaMemcpyDeviceToDevice, s);
   if (rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + pops, sbb, cudaMemcpyDeviceToDevice, s);
   void *own0 = ctx->f[0], *own1 = ctx->f[1];
   const int own_cur = ctx->cur;
-  // recompute: step i reads pool[i-1] and writes pool[i]
+  // recompute: step i reads slot i-1, writes slot i and captures the fields
+  // of state i-1 into slot i-1
   for (int i = 1; i < n; ++i) {
-    ctx->f[ctx->cur] = pool + (size_t)(i - 1) * sbytes;
-    ctx->f[1 - ctx->cur] = pool + (size_t)i * sbytes;
+    ctx->f[ctx->cur] = slot(i - 1);
+    ctx->f[1 - ctx->cur] = slot(i);
+    ctx->capture = (float *)(slot(i - 1) + cap_off);
     launch_step(ctx);
-    if (rest)
-      cudaMemcpyAsync(pool + (size_t)i * sbytes + pops, ctx->fld.sb, sbb, cudaMemcpyDeviceToDevice, s);
+    ctx->capture = nullptr;
+    if (rest) cudaMemcpyAsync(slot(i) + pops, ctx->fld.sb, sbb, cudaMemcpyDeviceToDevice, s);
   }
-  // adjoint steps from t0+n-1 down to t0, lambda ping-pong
+  // adjoint steps from t0+n-1 down to t0, lambda ping-pong; the last state
+  // of the segment was not stepped, so its fields are recomputed
   float *lin = lam, *lout = lam_tmp;
   for (int k = n - 1; k >= 0; --k) {
-    ctx->f[ctx->cur] = pool + (size_t)k * sbytes;
-    if (rest) cudaMemcpyAsync(ctx->fld.sb, pool + (size_t)k * sbytes + pops, sbb, cudaMemcpyDeviceToDevice, s);
+    ctx->f[ctx->cur] = slot(k);
     cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
-    launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, grad_params);
+    if (k == n - 1) {
+      if (rest) cudaMemcpyAsync(ctx->fld.sb, slot(k) + pops, sbb, cudaMemcpyDeviceToDevice, s);
+      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, grad_params);
+    } else {
+      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, grad_params, (const float *)(slot(k) + cap_off),
+                          rest ? (const float *)(slot(k) + pops) : ctx->fld.sb);
+    }
     float *t = lin;
     lin = lout;
     lout = t;

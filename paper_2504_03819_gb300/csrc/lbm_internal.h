@@ -90,6 +90,7 @@ struct lbm_ctx {
   int *scan;            // per-block counts of the boundary-list compaction
   void *f[2];
   int cur;
+  float *capture;       // when set, the fused step writes rho, mu', u, F, Q of its input state here (11 N floats)
   lbm::Fields fld;
   double *red_partial;  // RED_BLOCKS * 2
   lbm::AdjFields adj;   // adjoint scratch
@@ -137,7 +138,10 @@ void launch_get_populations(lbm_ctx *ctx, float *out);
 void launch_copy_mu(lbm_ctx *ctx, float *out);       // mu' + mu_ref
 void launch_fields_full(lbm_ctx *ctx);               // rho, j, mu', u, F, phi, Q of the current state
 void launch_moments_mu(lbm_ctx *ctx);                // rho, j, mu' (+ wetting) of the current state
-void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad);
+// captured: fields of f_state as written by the fused step (rho, mu', u, F,
+// Q; 11 N floats) with sb_state its shift bases, or null to recompute them
+void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad,
+                         const float *captured = nullptr, const float *sb_state = nullptr);
 void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0);
 void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad);
 void launch_set_populations(lbm_ctx *ctx, const float *in);

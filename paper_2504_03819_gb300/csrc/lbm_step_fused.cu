@@ -220,7 +220,7 @@ template <typename T, bool MASK, bool TMA>
 __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
-            float *__restrict__ sb, int *__restrict__ status, KParams kp, int TZ,
+            float *__restrict__ sb, int *__restrict__ status, float *__restrict__ cap, KParams kp, int TZ,
             const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
@@ -429,7 +429,15 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     }
     fields(z + 1, true);
     __syncthreads();
-    if (!active) continue;
+    if (!active) {
+      if (cap && inside) {  // solid node: its wetting rho and mu', no flow
+        cap[n] = S.rho[r4(z)][c1];
+        cap[N + n] = S.mu[r5(z)][(ty + 2) * H2X + tx + 2];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) cap[(2 + c) * N + n] = 0.0f;
+      }
+      continue;
+    }
 
     // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa phi_a(x + c_q), partial sums
     // per plane
@@ -454,6 +462,19 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     const float Fx = uF[3 * NT + t], Fy = uF[4 * NT + t], Fz = uF[5 * NT + t];
     const float r_own = S.rho[r4(z)][c1];
     const float mu_own = S.mu[r5(z)][(ty + 2) * H2X + tx + 2];
+    if (cap) {  // fields of this state for the adjoint: rho, mu', u, F, Q
+      cap[n] = r_own;
+      cap[N + n] = mu_own;
+      cap[2 * N + n] = ux;
+      cap[3 * N + n] = uy;
+      cap[4 * N + n] = uz;
+      cap[5 * N + n] = Fx;
+      cap[6 * N + n] = Fy;
+      cap[7 * N + n] = Fz;
+      cap[8 * N + n] = Qx;
+      cap[9 * N + n] = Qy;
+      cap[10 * N + n] = Qz;
+    }
     const float pm = pm_of(mu_own, kp);
     float om1 = kp.om[1];
     if (kp.nu > 0.0f) om1 = 1.0f / (r_own * kp.nu / pm + 0.5f);
@@ -493,20 +514,24 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   }
 }
 
-// planes per block of the z-marching kernels: the longest of 16, 8, 4, 2 that
-// still gives at least two blocks per SM (long columns amortise the halo
-// planes a block loads and computes before its first plane)
-int z_chunk(int xy_blocks, int nz) {
-  static int sms = 0;  // SM count of the device, read once
-  if (sms <= 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
+// Planes per block of a z-marching kernel.  Blocks run in waves of `slots`
+// (SMs x resident blocks per SM) and a block of tz planes costs about
+// tz + pro plane-times (pro: its prologue of halo planes), so the choice
+// minimises waves x (tz + pro): long columns amortise the prologue, short
+// ones fill the last wave.
+int z_chunk(int xy_blocks, int nz, int slots, int pro) {
+  int best = 1;
+  long long best_cost = -1;
+  for (int tz = 1; tz <= 64; tz *= 2) {
+    const long long blocks = (long long)xy_blocks * ((nz + tz - 1) / tz);
+    const long long cost = (blocks + slots - 1) / slots * (tz + pro);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = tz;
+    }
+    if (tz >= nz) break;
   }
-  for (int tz : {16, 8, 4, 2})
-    if ((long long)xy_blocks * ((nz + tz - 1) / tz) >= 2LL * sms) return tz;
-  return 1;
+  return best;
 }
 
 // The dynamic shared-memory limit is a per-device attribute of each kernel:
@@ -520,6 +545,44 @@ template <auto K> void ensure_smem(size_t bytes) {
     cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     done.fetch_or(bit);
   }
+}
+
+// SMs x resident blocks per SM of kernel K at this block size and dynamic
+// shared memory, once per device
+template <auto K> int resident_slots(int threads, size_t smem) {
+  static int cached[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  dev &= 63;
+  if (cached[dev] <= 0) {
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, K, threads, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    cached[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 152);
+  }
+  return cached[dev];
+}
+
+// the chemical-potential kernel: z-chunks sized by the same wave model
+void launch_mu_z(lbm_ctx *ctx) {
+  const KParams &kp = ctx->kp;
+  const int xyb = ((kp.nx + MX - 1) / MX) * ((kp.ny + MY - 1) / MY);
+  const int mz = z_chunk(xyb, kp.nz, resident_slots<k_mu_z>(MX * MY, 0), 2);
+  const dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + mz - 1) / mz);
+  k_mu_z<<<grid, MX * MY, 0, ctx->stream>>>(ctx->fld.rho, ctx->mask, ctx->fld.mu, kp, mz);
+}
+
+void launch_moments(lbm_ctx *ctx) {
+  const KParams &kp = ctx->kp;
+  const Fields &d = ctx->fld;
+  const int g = (kp.N + 255) / 256;
+  const void *fin = ctx->f[ctx->cur];
+  if (ctx->storage == LBM_F16)
+    k_moments_v<__half><<<g, 256, 0, ctx->stream>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status,
+                                                    kp);
+  else
+    k_moments_v<float><<<g, 256, 0, ctx->stream>>>((const float *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -567,82 +630,59 @@ const CUtensorMap *population_tmap(lbm_ctx *ctx, const void *p) {
   return e.ok ? &e.map : nullptr;
 }
 
-template <typename T>
-void launch_fused(lbm_ctx *ctx, const void *fin_v, void *fout_v) {
+template <typename T, bool MASK, bool TMA>
+void launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
   const KParams &kp = ctx->kp;
   const Fields &d = ctx->fld;
+  constexpr size_t sm = fused_smem_size<T>(TMA);
+  ensure_smem<k_fused<T, MASK, TMA>>(sm);
+  const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
+  const int tz = z_chunk(xyb, kp.nz, resident_slots<k_fused<T, MASK, TMA>>(NT, sm), 2);
+  const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
+  k_fused<T, MASK, TMA><<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j, d.mu, d.sb,
+                                                       ctx->status, ctx->capture, kp, tz, map);
+}
+
+template <typename T>
+void launch_fused(lbm_ctx *ctx, const void *fin_v, void *fout_v) {
   const T *fin = static_cast<const T *>(fin_v);
   T *fout = static_cast<T *>(fout_v);
-  const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
-  const int tz = z_chunk(xyb, kp.nz);
-  const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
   const CUtensorMap *map = population_tmap(ctx, fin_v);
-  cudaStream_t s = ctx->stream;
   if (map) {
-    constexpr size_t sm = fused_smem_size<T>(true);
-    if (ctx->mask) {
-      ensure_smem<k_fused<T, true, true>>(sm);
-      k_fused<T, true, true><<<grid, NT, sm, s>>>(fin, fout, ctx->mask, d.rho, d.j, d.mu, d.sb, ctx->status, kp, tz,
-                                                  *map);
-    } else {
-      ensure_smem<k_fused<T, false, true>>(sm);
-      k_fused<T, false, true><<<grid, NT, sm, s>>>(fin, fout, nullptr, d.rho, d.j, d.mu, d.sb, ctx->status, kp, tz,
-                                                   *map);
-    }
+    if (ctx->mask)
+      launch_fused_k<T, true, true>(ctx, fin, fout, *map);
+    else
+      launch_fused_k<T, false, true>(ctx, fin, fout, *map);
   } else {
     // rows that a tensor copy cannot describe: per-thread loads, the mask
     // checks compiled in (an all-fluid domain has an all-zero solid plane)
-    constexpr size_t sm = fused_smem_size<T>(false);
     static const CUtensorMap unused{};
-    ensure_smem<k_fused<T, true, false>>(sm);
-    k_fused<T, true, false><<<grid, NT, sm, s>>>(fin, fout, ctx->mask, d.rho, d.j, d.mu, d.sb, ctx->status, kp, tz,
-                                                 unused);
+    launch_fused_k<T, true, false>(ctx, fin, fout, unused);
   }
 }
 
 }  // namespace
 
 void launch_moments_mu(lbm_ctx *ctx) {
-  const KParams &kp = ctx->kp;
-  const Fields &d = ctx->fld;
-  cudaStream_t s = ctx->stream;
-  const int g = (kp.N + 255) / 256;
-  const void *fin = ctx->f[ctx->cur];
-  if (ctx->storage == LBM_F16)
-    k_moments_v<__half><<<g, 256, 0, s>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
-  else
-    k_moments_v<float><<<g, 256, 0, s>>>((const float *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
+  launch_moments(ctx);
   ctx->launches++;
   if (ctx->n_bnd) launch_wet_rho(ctx);
-  const int xyb = ((kp.nx + MX - 1) / MX) * ((kp.ny + MY - 1) / MY);
-  const int mz = z_chunk(xyb, kp.nz);
-  dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + mz - 1) / mz);
-  k_mu_z<<<grid, MX * MY, 0, s>>>(d.rho, ctx->mask, d.mu, kp, mz);
+  launch_mu_z(ctx);
   ctx->launches++;
   if (ctx->n_bnd) launch_wet_mu(ctx);
 }
 
 void launch_step_fused(lbm_ctx *ctx) {
-  const KParams &kp = ctx->kp;
-  const Fields &d = ctx->fld;
-  cudaStream_t s = ctx->stream;
-  const int g = (kp.N + 255) / 256;
   const void *fin = ctx->f[ctx->cur];
   void *fout = ctx->f[1 - ctx->cur];
   {
     TimedLaunch t(ctx, K_MOMENTS);
-    if (ctx->storage == LBM_F16)
-      k_moments_v<__half><<<g, 256, 0, s>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
-    else
-      k_moments_v<float><<<g, 256, 0, s>>>((const float *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
+    launch_moments(ctx);
   }
   if (ctx->n_bnd) launch_wet_rho(ctx);
   {
     TimedLaunch t(ctx, K_MU);
-    const int xyb = ((kp.nx + MX - 1) / MX) * ((kp.ny + MY - 1) / MY);
-    const int mz = z_chunk(xyb, kp.nz);
-    dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + mz - 1) / mz);
-    k_mu_z<<<grid, MX * MY, 0, s>>>(d.rho, ctx->mask, d.mu, kp, mz);
+    launch_mu_z(ctx);
   }
   if (ctx->n_bnd) launch_wet_mu(ctx);
   {

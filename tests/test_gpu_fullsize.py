@@ -9,8 +9,8 @@ the collision at x - c_q, which reads rho up to three nodes further through
 mu, grad mu, phi and Q; next to walls the wetting averages add one node per
 stage), so the oracle steps a periodic sub-box of half-width R around each
 sampled node, cut from the same input, and its centre must equal the GPU's
-value.  Samples include tile edges and corners (32 x 8 columns) and the
-first and last planes of the z chunks of the fused kernel.
+value.  Samples include tile edges and corners of the column tiles and the
+first and last planes of the z chunks of the fused kernel (8 to 32 planes).
 """
 import numpy as np
 import pytest
@@ -44,9 +44,9 @@ def samples(n, rng, extra):
     """Tile-edge / chunk-edge positions plus seeded random ones, as (x, y, z)."""
     nx, ny, nz = n
     edge_x = [0, 31, 32, nx - 1]
-    edge_y = [0, 7, 8, ny - 1]
-    edge_z = [0, 15, 16, nz - 1]
-    pts = [(edge_x[i % 4], edge_y[(i // 4) % 4], edge_z[(i * 3 + i // 4) % 4]) for i in range(16)]
+    edge_y = [0, 3, 4, 7, 8, ny - 1]
+    edge_z = [0, 7, 8, 15, 16, 31, 32, nz - 1]
+    pts = [(edge_x[i % 4], edge_y[(i // 4) % 6], edge_z[(i * 5 + i // 8) % 8]) for i in range(24)]
     pts += [tuple(int(v) for v in rng.integers(0, (nx, ny, nz))) for _ in range(extra)]
     return pts
 
