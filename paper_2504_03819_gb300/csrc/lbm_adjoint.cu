@@ -18,10 +18,13 @@
 //                       per-node omega_1 (Sec. II B) transposed
 //   k_adj_mu            grad mu transposed (a gather) + the local p_m term
 //   k_adj_wet_mu        Eq. 36 transposed (solid -> fluid neighbours)
-//   k_adj_rho           mu = mu0(rho) - kappa lap rho (Eqs. 2, 32) transposed
-//   k_adj_wet_prep /    Eqs. 37-38 transposed (branch of the forward pass:
-//   k_adj_out           clamped densities pass no gradient), then
-//                       lambda_q(t) = local part + lambda_rho + c_q . lambda_j
+//   k_adj_rho           mu = mu0(rho) - kappa lap rho (Eqs. 2, 32) transposed,
+//                       Eqs. 37-38 transposed at solid boundary nodes (branch
+//                       of the forward pass: clamped densities pass no
+//                       gradient), and lambda_q(t) = local part + lambda_rho
+//                       + c_q . lambda_j at fluid nodes away from walls
+//   k_adj_out_wall      the same output at fluid nodes next to walls, with
+//                       the wetting gather
 //
 // Parameter gradients are summed per block in FP64 and reduced in a fixed
 // order (deterministic).
@@ -310,8 +313,9 @@ __device__ __forceinline__ Site site_of(const KParams &kp) {
 
 __device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
-// block sum of NPAR values into partial[block_id() * NPAR + i]: a shuffle
-// tree per warp, then the warps in order (fixed order: deterministic)
+// block sum of NPAR values added to partial[block_id() * NPAR + i]: a
+// shuffle tree per warp, then the warps in order (fixed order: deterministic;
+// the partials accumulate over launches until the caller reduces them)
 __device__ void block_partials(double v[NPAR], double *partial) {
   constexpr int MAXW = 8;
   __shared__ double sm[NPAR][MAXW];
@@ -328,7 +332,7 @@ __device__ void block_partials(double v[NPAR], double *partial) {
   if (t < NPAR) {
     double acc = 0.0;
     for (int w = 0; w < nw; ++w) acc += sm[t][w];
-    partial[(size_t)block_id() * NPAR + t] = acc;
+    partial[(size_t)block_id() * NPAR + t] += acc;
   }
 }
 
@@ -357,7 +361,6 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(con
       a.om1[n] = 0.0f;
       a.rho[n] = 0.0f;
     } else {
-      a.rho[n] = 0.0f;  // direct density adjoint: none in a step
       const bool rest = kp.shift_mode == LBM_SHIFT_REST;
       const float rb = rest ? sb[n] : kp.rho_shift, cb = rest ? sb[N + n] : 0.0f;
       auto load_f = [&](float f[27]) {
@@ -413,6 +416,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(con
       a.Q[N + n] = lQy;
       a.Q[2 * N + n] = lQz;
       a.pm[n] = lpm;
+      a.rho[n] = 0.0f;  // direct density adjoint: none in a step
       if (kp.nu > 0.0f) {
         a.om1[n] = lom1;
       } else {
@@ -477,11 +481,15 @@ __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ 
     lrho += lo * (-om1 * om1 * kp.nu / pm);
     lpm += lo * (om1 * om1 * r * kp.nu / (pm * pm));
   }
-  // u = (j + F/2)/rho, F = (1/3 - rho) g
+  // u = (j + F/2)/rho, F = (1/3 - rho) g; every input is read before the
+  // first store (the adjoint arrays share no restrict guarantee)
   const float ir = 1.0f / r;
+  const float lFin[3] = {a.F[n], a.F[N + n], a.F[2 * N + n]};
+  const float lrho0 = a.rho[n];
   float udot = 0.0f, Fdotg = 0.0f;
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const float lF = a.F[c * N + n] + 0.5f * lu[c] * ir;
+    const float lF = lFin[c] + 0.5f * lu[c] * ir;
     udot += lu[c] * u[c];
     const float g = F[c] / c3;  // grad mu recovered from F (rho != 1/3 on fluid nodes)
     Fdotg += lF * g;
@@ -489,7 +497,7 @@ __global__ void __launch_bounds__(256) k_adj_fields(const uint8_t *__restrict__ 
     a.u[c * N + n] = lu[c] * ir;  // lj
   }
   lrho += -udot * ir - Fdotg;
-  a.rho[n] += lrho;  // adds to any direct seed
+  a.rho[n] = lrho0 + lrho;  // adds to any direct seed
   a.mu[n] = lpm * (1.0f / 3.0f);
 }
 
@@ -537,11 +545,32 @@ __global__ void __launch_bounds__(256) k_adj_wet_mu(const uint8_t *__restrict__ 
   a.mu[n] = a.pm[n] + add;  // final lmu on fluid nodes into a.mu
 }
 
+// lambda_q(t)(n) += lrho + c_q . lj with lj = a.u(n): all 27 loads are
+// issued before the first store (stores to one plane could otherwise alias
+// the loads of the next and serialise them)
+__device__ __forceinline__ void add_output(float *__restrict__ lam_t, int n, size_t N, float lr, const AdjFields &a) {
+  const float jx = a.u[n], jy = a.u[N + n], jz = a.u[2 * N + n];
+  float v[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) v[q] = lam_t[q * N + n];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) lam_t[q * N + n] = v[q] + (lr + cx_of(q) * jx + cy_of(q) * jy + cz_of(q) * jz);
+}
+
 // mu(x) = mu0(rho(x)) - kappa 6 (sum_q w_q rho(x+c_q) - rho(x)) on fluid x:
 // lrho(y) += [fluid y] (mu0'(rho) + 6 kappa) lmu(y) - 6 kappa sum_q w_q lmu(y+c_q)
 // and dJ/dkappa += -sum_fluid lmu(x) 6 (sum_q w_q rho(x+c_q) - rho(x)).
+// lrho goes to a.phi.  Then, per node:
+//  - solid boundary node b: Eqs. 37-38 transposed, part 1: the derivative of
+//    the solid density with respect to rho_ave (1, phi, or 0 when clamped)
+//    and to the wetting value; dJ/d value += lrho(b) d rho_s / d value, and
+//    a.F[b] = (d rho_s / d rho_ave) lrho(b) / den(b) for the fluid gather;
+//  - fluid node with no solid neighbour, when lam_t is given: the output
+//    lambda_q(t) += lrho + c_q . lj (nodes next to walls finish in
+//    k_adj_out_wall, once every a.F[b] exists).
 __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
-                                                 Fields d, AdjFields a, const float *__restrict__ lmu,
+                                                 const float *__restrict__ inv_den, Fields d, AdjFields a,
+                                                 const float *__restrict__ lmu, float *__restrict__ lam_t,
                                                  double *__restrict__ partial, KParams kp) {
   const Site st = site_of(kp);
   const int n = st.n;
@@ -570,81 +599,58 @@ __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mas
       lr = a.rho[n] + dmu0 * l0 - 6.0f * kp.kappa * (s + weight_of(13) * l0 - l0);
       par[0] = -(double)l0 * 6.0 * (double)lap;
     }
+    if (solid && inv_den[n] > 0.0f) {
+      // rho_ave formed exactly as the forward k_wet_rho forms it
+      float num = 0.0f, den = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        if (q == 13 || ((sn >> q) & 1u)) continue;
+        num += weight_of(q) * d.rho[st.at(cx_of(q), cy_of(q), cz_of(q))];
+        den += weight_of(q);
+      }
+      const float ave = num / den;
+      float dave = 1.0f, dval = 0.0f;
+      if (kp.wet_mode != LBM_WET_NEUTRAL && ave >= kp.band_lo && ave <= kp.band_hi) {
+        const float mv = kp.wet_mode == LBM_WET_PHI ? kp.wet_value * ave : ave - kp.wet_value;
+        if (mv < kp.band_lo || mv > kp.band_hi) {
+          dave = 0.0f;
+        } else if (kp.wet_mode == LBM_WET_PHI) {
+          dave = kp.wet_value;
+          dval = ave;
+        } else {
+          dave = 1.0f;
+          dval = -1.0f;
+        }
+      }
+      par[12] = (double)lr * dval;
+      a.F[n] = dave / den * lr;  // scaled adjoint handed to the fluid neighbours
+    } else if (!solid && sn == 0u && lam_t) {
+      add_output(lam_t, n, (size_t)kp.N, lr, a);
+    }
     a.phi[n] = lr;  // total lrho into a.phi[0..N)
   }
   block_partials(par, partial);
 }
 
-// Eqs. 37-38 transposed, part 1 on the boundary list: the derivative of the
-// solid density with respect to rho_ave (1, phi, or 0 when clamped) and to the
-// wetting value, and the parameter gradient lrho(b) * d rho_s / d value.
-__global__ void __launch_bounds__(BLK) k_adj_wet_prep(const int *__restrict__ bnd, int nb,
-                                                      const uint32_t *__restrict__ nbr, Fields d, AdjFields a,
-                                                      double *__restrict__ partial, KParams kp) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double par[NPAR];
-#pragma unroll
-  for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
-  if (t < nb) {
-    const int b = bnd[t];
-    const Node p = decode(b, kp.nx, kp.ny);
-    const uint32_t solid = nbr[b];
-    float num = 0.0f, den = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      if (q == 13) continue;
-      if (!((solid >> q) & 1u)) {
-        num += weight_of(q) * d.rho[neighbour(p, cx_of(q), cy_of(q), cz_of(q), kp)];
-        den += weight_of(q);
-      }
-    }
-    const float ave = num / den;
-    float dave = 1.0f, dval = 0.0f;
-    if (kp.wet_mode != LBM_WET_NEUTRAL && ave >= kp.band_lo && ave <= kp.band_hi) {
-      const float m = kp.wet_mode == LBM_WET_PHI ? kp.wet_value * ave : ave - kp.wet_value;
-      if (m < kp.band_lo || m > kp.band_hi) {
-        dave = 0.0f;
-      } else if (kp.wet_mode == LBM_WET_PHI) {
-        dave = kp.wet_value;
-        dval = ave;
-      } else {
-        dave = 1.0f;
-        dval = -1.0f;
-      }
-    }
-    const float lrs = a.phi[b];
-    par[12] = (double)lrs * dval;
-    a.F[b] = dave / den * lrs;  // scaled adjoint handed to the fluid neighbours
-  }
-  block_partials(par, partial);
-}
-
-// lambda_q(t)(x) = local part + lrho(x) + c_q . lj(x) on fluid nodes, with
-// part 2 of Eqs. 37-38 transposed when there are walls: lrho(y) += sum over
-// solid neighbours b of w_q (dave(b)/den(b)) lrho(b) (stored in a.F).
-__global__ void __launch_bounds__(256) k_adj_out(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
-                                                 int wet, AdjFields a, float *__restrict__ lam_t, KParams kp) {
+// lambda_q(t)(x) += lrho(x) + c_q . lj(x) at fluid nodes next to walls, with
+// part 2 of Eqs. 37-38 transposed: lrho(y) += sum over solid neighbours b of
+// w_q (dave(b)/den(b)) lrho(b) (stored in a.F by k_adj_rho)
+__global__ void __launch_bounds__(256) k_adj_out_wall(const uint8_t *__restrict__ mask,
+                                                      const uint32_t *__restrict__ nbr, AdjFields a,
+                                                      float *__restrict__ lam_t, KParams kp) {
   const Site st = site_of(kp);
   if (!st.in) return;
   const int n = st.n;
-  if (mask && mask[n]) return;
+  const uint32_t solid = nbr[n];
+  if (mask[n] || solid == 0u) return;
   const size_t N = (size_t)kp.N;
   float lr = a.phi[n];
-  if (wet) {
-    // solid neighbours b = n + c_p (bit p); a.F[b] = dave(b)/den(b) lrho(b)
-    const uint32_t solid = nbr[n];
-    if (solid) {
 #pragma unroll
-      for (int p = 0; p < 27; ++p) {
-        if (p == 13 || !((solid >> p) & 1u)) continue;
-        lr += weight_of(p) * a.F[st.at(cx_of(p), cy_of(p), cz_of(p))];
-      }
-    }
+  for (int p = 0; p < 27; ++p) {
+    if (p == 13 || !((solid >> p) & 1u)) continue;
+    lr += weight_of(p) * a.F[st.at(cx_of(p), cy_of(p), cz_of(p))];
   }
-  const float jx = a.u[n], jy = a.u[N + n], jz = a.u[2 * N + n];
-#pragma unroll
-  for (int q = 0; q < 27; ++q)
-    lam_t[q * N + n] += lr + cx_of(q) * jx + cy_of(q) * jy + cz_of(q) * jz;
+  add_output(lam_t, n, N, lr, a);
 }
 
 // adds the NPAR block partials of `blocks` blocks into out[0..NPAR): one
@@ -816,14 +822,12 @@ __global__ void __launch_bounds__(256) k_obj_seed(int kind, int wall_z, const ui
   }
 }
 
-}  // namespace
-
-// Parameter partials: region 0 (collision), region 1 (mu -> rho), region 2
-// (wetting) lie back to back in ctx->adj_partial and are summed by one
-// k_adj_reduce over all their blocks.
+// Parameter partials: region 0 (collision) and region 1 (mu -> rho, with the
+// wetting transpose) lie back to back in ctx->adj_partial.  Kernels add to
+// them; launch_adjoint_partials_reduce sums both regions into the gradient.
 struct Regions {
-  double *collide, *rho, *wet;
-  int gb, gw;
+  double *collide, *rho;
+  int gb;
 };
 
 // 3-D launch shape of the node-parallel kernels: 32 x by threads per block
@@ -832,22 +836,21 @@ dim3 grid3(const lbm_ctx *ctx, int by) { return dim3((ctx->nx + 31) / 32, (ctx->
 Regions regions(lbm_ctx *ctx) {
   Regions r;
   r.gb = (int)adj_blocks(ctx->nx, ctx->ny, ctx->nz);
-  r.gw = ctx->n_bnd ? (ctx->n_bnd + BLK - 1) / BLK : 0;
   r.collide = ctx->adj_partial;
   r.rho = ctx->adj_partial + (size_t)r.gb * NPAR;
-  r.wet = ctx->adj_partial + (size_t)2 * r.gb * NPAR;
   return r;
 }
 
-// mu -> rho transpose, wetting part 1, and the output kernel shared by the
-// three entry points; lmu is the final adjoint of mu on fluid nodes
-void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R, const Fields &d) {
+// mu -> rho transpose with the wetting transpose and, when lam_t is given,
+// the output lambda(t) (bulk nodes in k_adj_rho, nodes next to walls after)
+void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R, const Fields &d, float *lam_t) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
-  k_adj_rho<<<grid3(ctx, ADJ_BY), dim3(32, ADJ_BY), 0, s>>>(ctx->mask, ctx->nbr, d, ctx->adj, lmu, R.rho, kp);
+  k_adj_rho<<<grid3(ctx, ADJ_BY), dim3(32, ADJ_BY), 0, s>>>(ctx->mask, ctx->nbr, ctx->inv_den, d, ctx->adj, lmu,
+                                                            lam_t, R.rho, kp);
   ctx->launches++;
-  if (ctx->n_bnd) {
-    k_adj_wet_prep<<<R.gw, BLK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, d, ctx->adj, R.wet, kp);
+  if (lam_t && ctx->n_bnd) {
+    k_adj_out_wall<<<grid3(ctx, 8), dim3(32, 8), 0, s>>>(ctx->mask, ctx->nbr, ctx->adj, lam_t, kp);
     ctx->launches++;
   }
 }
@@ -863,6 +866,19 @@ const float *adj_mu(lbm_ctx *ctx) {
   return ctx->adj.mu;
 }
 
+}  // namespace
+
+void launch_adjoint_partials_zero(lbm_ctx *ctx) {
+  const Regions R = regions(ctx);
+  cudaMemsetAsync(ctx->adj_partial, 0, (size_t)2 * R.gb * NPAR * sizeof(double), ctx->stream);
+}
+
+void launch_adjoint_partials_reduce(lbm_ctx *ctx, double *grad) {
+  const Regions R = regions(ctx);
+  k_adj_reduce<<<NPAR, RB, 0, ctx->stream>>>(ctx->adj_partial, 2 * R.gb, grad);
+  ctx->launches++;
+}
+
 void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
@@ -871,11 +887,11 @@ void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, doubl
   // fields of the initial density are in ctx->fld (lbm_set_state ran before)
   k_adj_init<<<g, 256, 0, s>>>(ctx->mask, u0, lam0, ctx->fld, ctx->adj, kp);
   ctx->launches++;
-  cudaMemsetAsync(R.collide, 0, (size_t)R.gb * NPAR * sizeof(double), s);
-  adj_tail(ctx, ctx->adj.mu, R, ctx->fld);
-  k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
+  launch_adjoint_partials_zero(ctx);
+  adj_tail(ctx, ctx->adj.mu, R, ctx->fld, nullptr);
+  launch_adjoint_partials_reduce(ctx, grad);
   k_adj_grad_rho0<<<g, 256, 0, s>>>(ctx->mask, ctx->n_bnd ? 1 : 0, ctx->adj, grad_rho0, kp);
-  ctx->launches += 2;
+  ctx->launches++;
 }
 
 void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad) {
@@ -885,6 +901,7 @@ void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam,
   const Regions R = regions(ctx);
   const float rl = (float)ctx->params.rho_l, rv = (float)ctx->params.rho_v;
   launch_fields_full(ctx);
+  launch_adjoint_partials_zero(ctx);
   k_obj_sums<<<R.gb, BLK, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj_partial, kp, rv);
   k_obj_finish<<<1, RB, 0, s>>>(kind, ctx->adj_partial, R.gb, J, rl, rv);
   k_obj_seed<<<g, 256, 0, s>>>(kind, wall_z, ctx->mask, ctx->fld, ctx->adj, J, kp, rl, rv);
@@ -894,17 +911,12 @@ void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam,
   ctx->launches++;
   const float *lmu = adj_mu(ctx);
   // the objective's direct dependence on kappa and on the wetting value
-  cudaMemsetAsync(R.collide, 0, (size_t)R.gb * NPAR * sizeof(double), s);
-  adj_tail(ctx, lmu, R, ctx->fld);
-  if (grad) {
-    k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
-    ctx->launches++;
-  }
-  k_adj_out<<<grid3(ctx, 8), dim3(32, 8), 0, s>>>(ctx->mask, ctx->nbr, ctx->n_bnd ? 1 : 0, ctx->adj, lam, kp);
-  ctx->launches++;
+  launch_adjoint_partials_zero(ctx);
+  adj_tail(ctx, lmu, R, ctx->fld, lam);
+  if (grad) launch_adjoint_partials_reduce(ctx, grad);
 }
 
-void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad,
+void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t,
                          const float *captured, const float *sb_state) {
   const KParams &kp = ctx->kp;
   cudaStream_t s = ctx->stream;
@@ -932,10 +944,7 @@ void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_nex
   k_adj_fields<<<g8, b8, 0, s>>>(ctx->mask, d, ctx->adj, kp);
   ctx->launches += 2;
   const float *lmu = adj_mu(ctx);
-  adj_tail(ctx, lmu, R, d);
-  k_adj_reduce<<<NPAR, RB, 0, s>>>(ctx->adj_partial, 2 * R.gb + R.gw, grad);
-  k_adj_out<<<g8, b8, 0, s>>>(ctx->mask, ctx->nbr, ctx->n_bnd ? 1 : 0, ctx->adj, lam_t, kp);
-  ctx->launches += 2;
+  adj_tail(ctx, lmu, R, d, lam_t);
 }
 
 }  // namespace lbm

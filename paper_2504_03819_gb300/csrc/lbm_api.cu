@@ -25,7 +25,7 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 //                   fluid-weight sums, N/256 + 2 ints of compaction counts
 //   reduction       RED_BLOCKS * 2 doubles
 //   status          2 ints
-//   adjoint         16 N floats, then 3 regions of adj_blocks() blocks x
+//   adjoint         16 N floats, then 2 regions of adj_blocks() blocks x
 //                   LBM_NGRAD doubles of gradient partials
 struct Layout {
   size_t f0, f1, fields, bnd, nbr, inv_den, scan, red, status, adj, adj_partial, total;
@@ -48,7 +48,7 @@ bool layout(int nx, int ny, int nz, int storage, Layout *L) {
   L->red = off; off = align_up(off + (size_t)RED_BLOCKS * 2 * sizeof(double));
   L->status = off; off = align_up(off + 2 * sizeof(int));
   L->adj = off; off = align_up(off + 16 * (size_t)N * sizeof(float));
-  L->adj_partial = off; off = align_up(off + 3 * adj_blocks(nx, ny, nz) * LBM_NGRAD * sizeof(double));
+  L->adj_partial = off; off = align_up(off + 2 * adj_blocks(nx, ny, nz) * LBM_NGRAD * sizeof(double));
   L->total = off;
   return true;
 }
@@ -366,7 +366,9 @@ int lbm_adjoint_step(lbm_ctx *ctx, const void *state_t, const float *lam_next, f
     return LBM_ERR_ARG;
   int rc = lbm_set_raw_state(ctx, state_t);
   if (rc != LBM_OK) return rc;
-  launch_adjoint_step(ctx, ctx->f[ctx->cur], lam_next, lam_t, grad_params);
+  launch_adjoint_partials_zero(ctx);
+  launch_adjoint_step(ctx, ctx->f[ctx->cur], lam_next, lam_t);
+  launch_adjoint_partials_reduce(ctx, grad_params);
   return check_cuda(ctx, "lbm_adjoint_step");
 }
 
@@ -405,20 +407,22 @@ int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool,
   // adjoint steps from t0+n-1 down to t0, lambda ping-pong; the last state
   // of the segment was not stepped, so its fields are recomputed
   float *lin = lam, *lout = lam_tmp;
+  launch_adjoint_partials_zero(ctx);  // the segment's gradient partials accumulate over its steps
   for (int k = n - 1; k >= 0; --k) {
     ctx->f[ctx->cur] = slot(k);
     cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
     if (k == n - 1) {
       if (rest) cudaMemcpyAsync(ctx->fld.sb, slot(k) + pops, sbb, cudaMemcpyDeviceToDevice, s);
-      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, grad_params);
+      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout);
     } else {
-      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, grad_params, (const float *)(slot(k) + cap_off),
+      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, (const float *)(slot(k) + cap_off),
                           rest ? (const float *)(slot(k) + pops) : ctx->fld.sb);
     }
     float *t = lin;
     lin = lout;
     lout = t;
   }
+  launch_adjoint_partials_reduce(ctx, grad_params);
   if (lin != lam) cudaMemcpyAsync(lam, lin, 27 * (size_t)ctx->N * sizeof(float), cudaMemcpyDeviceToDevice, s);
   // the context's own buffers hold ckpt afterwards
   ctx->f[0] = own0;

@@ -138,10 +138,15 @@ void launch_get_populations(lbm_ctx *ctx, float *out);
 void launch_copy_mu(lbm_ctx *ctx, float *out);       // mu' + mu_ref
 void launch_fields_full(lbm_ctx *ctx);               // rho, j, mu', u, F, phi, Q of the current state
 void launch_moments_mu(lbm_ctx *ctx);                // rho, j, mu' (+ wetting) of the current state
-// captured: fields of f_state as written by the fused step (rho, mu', u, F,
-// Q; 11 N floats) with sb_state its shift bases, or null to recompute them
-void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t, double *grad,
+// One adjoint step; its parameter-gradient partials are added to
+// ctx->adj_partial (zeroed and reduced into the gradient by the two calls
+// below, once per step or once per checkpoint segment).  captured: fields of
+// f_state as written by the fused step (rho, mu', u, F, Q; 11 N floats) with
+// sb_state its shift bases, or null to recompute them.
+void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_next, float *lam_t,
                          const float *captured = nullptr, const float *sb_state = nullptr);
+void launch_adjoint_partials_zero(lbm_ctx *ctx);
+void launch_adjoint_partials_reduce(lbm_ctx *ctx, double *grad);
 void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0);
 void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad);
 void launch_set_populations(lbm_ctx *ctx, const float *in);
