@@ -313,10 +313,34 @@ __device__ __forceinline__ Site site_of(const KParams &kp) {
 
 __device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
-// block sum of NPAR values added to partial[block_id() * NPAR + i]: a
-// shuffle tree per warp, then the warps in order (fixed order: deterministic;
-// the partials accumulate over launches until the caller reduces them)
-__device__ void block_partials(double v[NPAR], double *partial) {
+// Block sums of M FP32 per-node values, added to the parameter slots
+// slot[0..M) of partial[block_id() * NPAR + ...]: a fixed FP32 shuffle tree
+// per warp (the per-node contributions are FP32), then the warp sums in FP64
+// in warp order.  Deterministic; the partials accumulate over launches until
+// the caller reduces them.
+template <int M>
+__device__ void block_partials(float (&v)[M], const int (&slot)[M], double *partial) {
+  constexpr int MAXW = 8;
+  __shared__ float sm[M][MAXW];
+  const int t = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nw = (blockDim.x * blockDim.y) / 32;
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+  if ((t & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < M; ++i) sm[i][t >> 5] = v[i];
+  __syncthreads();
+  if (t < M) {
+    double acc = 0.0;
+    for (int w = 0; w < nw; ++w) acc += (double)sm[t][w];
+    partial[(size_t)block_id() * NPAR + slot[t]] += acc;
+  }
+}
+
+// the same with FP64 per-node values in every slot (objective sums)
+__device__ void block_partials_f64(double (&v)[NPAR], double *partial) {
   constexpr int MAXW = 8;
   __shared__ double sm[NPAR][MAXW];
   const int t = threadIdx.x + blockDim.x * threadIdx.y;
@@ -348,9 +372,9 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(con
                                                      Fields d, AdjFields a, double *__restrict__ partial, KParams kp) {
   const Site st = site_of(kp);
   const int n = st.n;
-  double par[NPAR];
+  float pg[11];  // dJ/d omega_0..omega_10 of this node
 #pragma unroll
-  for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
+  for (int i = 0; i < 11; ++i) pg[i] = 0.0f;
   const size_t N = (size_t)kp.N;
   if (st.in) {
     if (mask && mask[n]) {
@@ -424,10 +448,11 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(con
         gom[1] = lom1;
       }
 #pragma unroll
-      for (int i = 0; i < 11; ++i) par[1 + i] = gom[i];
+      for (int i = 0; i < 11; ++i) pg[i] = gom[i];
     }
   }
-  block_partials(par, partial);
+  const int slots[11] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11};
+  block_partials(pg, slots, partial);
 }
 
 // local field adjoints at a fluid node.  First lphi(x) by the transposed
@@ -574,9 +599,7 @@ __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mas
                                                  double *__restrict__ partial, KParams kp) {
   const Site st = site_of(kp);
   const int n = st.n;
-  double par[NPAR];
-#pragma unroll
-  for (int i = 0; i < NPAR; ++i) par[i] = 0.0;
+  float pg[2] = {0.0f, 0.0f};  // dJ/d kappa, dJ/d wetting value of this node
   if (st.in) {
     const bool solid = mask && mask[n];  // lmu: final lmu on fluid nodes; solid entries are not read
     const uint32_t sn = mask ? nbr[n] : 0u;
@@ -597,7 +620,7 @@ __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mas
       const float om = 1.0f - kp.b * r;
       const float dmu0 = kp.RT * (1.0f / r + kp.b / om + kp.b / (om * om)) - 2.0f * kp.a;
       lr = a.rho[n] + dmu0 * l0 - 6.0f * kp.kappa * (s + weight_of(13) * l0 - l0);
-      par[0] = -(double)l0 * 6.0 * (double)lap;
+      pg[0] = -6.0f * l0 * lap;
     }
     if (solid && inv_den[n] > 0.0f) {
       // rho_ave formed exactly as the forward k_wet_rho forms it
@@ -622,14 +645,15 @@ __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mas
           dval = -1.0f;
         }
       }
-      par[12] = (double)lr * dval;
+      pg[1] = lr * dval;
       a.F[n] = dave / den * lr;  // scaled adjoint handed to the fluid neighbours
     } else if (!solid && sn == 0u && lam_t) {
       add_output(lam_t, n, (size_t)kp.N, lr, a);
     }
     a.phi[n] = lr;  // total lrho into a.phi[0..N)
   }
-  block_partials(par, partial);
+  const int slots[2] = {0, 12};
+  block_partials(pg, slots, partial);
 }
 
 // lambda_q(t)(x) += lrho(x) + c_q . lj(x) at fluid nodes next to walls, with
@@ -759,7 +783,7 @@ __global__ void __launch_bounds__(BLK) k_obj_sums(int kind, int wall_z, const ui
       par[0] = (double)(r - rho_v);
     }
   }
-  block_partials(par, partial);
+  block_partials_f64(par, partial);
 }
 
 __global__ void __launch_bounds__(RB) k_obj_finish(int kind, const double *__restrict__ partial, int blocks,
