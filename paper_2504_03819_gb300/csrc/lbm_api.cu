@@ -212,7 +212,14 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
   k.a = (float)p->a;
   k.b = (float)p->b;
   k.kappa = (float)p->kappa;
-  for (int i = 0; i < 11; ++i) k.om[i] = (float)p->omega[i];
+  for (int i = 0; i < 11; ++i) {
+    k.om[i] = (float)p->omega[i];
+    k.om_c[i] = 1.0f - k.om[i];
+    k.om_h[i] = 1.0f - 0.5f * k.om[i];
+  }
+  k.g3 = 2.0f * k.om_h[3] * (1.0f / 3.0f);
+  k.g5 = k.om_h[9] * (1.0f / 3.0f) * (1.0f / 3.0f);
+  k.o10e = k.om[10] * (1.0f / 3.0f) * (1.0f / 3.0f);
   k.nu = (float)p->nu;
   k.q4 = p->q4_correction;
   k.rho_shift = (float)p->rho_shift;

@@ -18,6 +18,8 @@ struct KParams {
   int nx, ny, nz, N;
   float RT, a, b, kappa;
   float om[11];
+  float om_c[11], om_h[11];  // 1 - omega_i and 1 - omega_i / 2 (collision factors)
+  float g3, g5, o10e;        // 2 (1 - omega_3/2) / 3, (1 - omega_9/2) / 9, omega_10 / 9
   float nu;        // > 0: omega_1 per node from 1/omega_1 = rho nu / p_m + 1/2
   int q4;          // fourth-order correction on/off
   float rho_shift; // rho_0 of the stored populations f_i - w_i rho_0

@@ -136,77 +136,72 @@ __device__ __forceinline__ void from_central(float k[27], float ux, float uy, fl
 #define KM(a, b, c) k[(a) + 3 * (b) + 9 * (c)]
 
 // Post-collision central moments, Eqs. 21-26, in place.  k000 is unchanged.
-// om1 is omega_1 of this node; the other rates come from kp.om.
+// om1 is omega_1 of this node; the other rates enter through the factors
+// 1 - omega_i, 1 - omega_i/2 and the forcing / equilibrium coefficients
+// precomputed in kp.
 __device__ __forceinline__ void collide_cm(float k[27], float pm, float Fx, float Fy, float Fz,
                                            float Qx, float Qy, float Qz, float om1,
                                            const KParams &kp) {
-  const float cs2 = 1.0f / 3.0f;
-  const float o0 = kp.om[0], o2 = kp.om[2], o3 = kp.om[3], o4 = kp.om[4], o5 = kp.om[5];
-  const float o6 = kp.om[6], o7 = kp.om[7], o8 = kp.om[8], o9 = kp.om[9], o10 = kp.om[10];
+  const float c1 = 1.0f - om1, h1 = 1.0f - 0.5f * om1;
   // first order (Eq. 21)
-  KM(1, 0, 0) = (1.0f - o0) * KM(1, 0, 0) + (1.0f - 0.5f * o0) * Fx;
-  KM(0, 1, 0) = (1.0f - o0) * KM(0, 1, 0) + (1.0f - 0.5f * o0) * Fy;
-  KM(0, 0, 1) = (1.0f - o0) * KM(0, 0, 1) + (1.0f - 0.5f * o0) * Fz;
+  KM(1, 0, 0) = kp.om_c[0] * KM(1, 0, 0) + kp.om_h[0] * Fx;
+  KM(0, 1, 0) = kp.om_c[0] * KM(0, 1, 0) + kp.om_h[0] * Fy;
+  KM(0, 0, 1) = kp.om_c[0] * KM(0, 0, 1) + kp.om_h[0] * Fz;
   // second order (Eq. 22)
-  KM(1, 1, 0) *= (1.0f - om1);
-  KM(0, 1, 1) *= (1.0f - om1);
-  KM(1, 0, 1) *= (1.0f - om1);
+  KM(1, 1, 0) *= c1;
+  KM(0, 1, 1) *= c1;
+  KM(1, 0, 1) *= c1;
   {
-    float A = (1.0f - om1) * (KM(2, 0, 0) - KM(0, 2, 0)) + (1.0f - 0.5f * om1) * (Qx - Qy);
-    float B = (1.0f - om1) * (KM(2, 0, 0) - KM(0, 0, 2)) + (1.0f - 0.5f * om1) * (Qx - Qz);
-    float S = (1.0f - o2) * (KM(2, 0, 0) + KM(0, 2, 0) + KM(0, 0, 2)) + 3.0f * o2 * pm +
-              (1.0f - 0.5f * o2) * (Qx + Qy + Qz);
+    float A = c1 * (KM(2, 0, 0) - KM(0, 2, 0)) + h1 * (Qx - Qy);
+    float B = c1 * (KM(2, 0, 0) - KM(0, 0, 2)) + h1 * (Qx - Qz);
+    float S = kp.om_c[2] * (KM(2, 0, 0) + KM(0, 2, 0) + KM(0, 0, 2)) + 3.0f * kp.om[2] * pm +
+              kp.om_h[2] * (Qx + Qy + Qz);
     KM(2, 0, 0) = (S + A + B) * (1.0f / 3.0f);
     KM(0, 2, 0) = (S - 2.0f * A + B) * (1.0f / 3.0f);
     KM(0, 0, 2) = (S + A - 2.0f * B) * (1.0f / 3.0f);
   }
   // third order (Eq. 23)
   {
-    const float g3 = 2.0f * (1.0f - 0.5f * o3) * cs2;
     float P, D;
-    P = (1.0f - o3) * (KM(1, 2, 0) + KM(1, 0, 2)) + g3 * Fx;
-    D = (1.0f - o4) * (KM(1, 2, 0) - KM(1, 0, 2));
+    P = kp.om_c[3] * (KM(1, 2, 0) + KM(1, 0, 2)) + kp.g3 * Fx;
+    D = kp.om_c[4] * (KM(1, 2, 0) - KM(1, 0, 2));
     KM(1, 2, 0) = 0.5f * (P + D);
     KM(1, 0, 2) = 0.5f * (P - D);
-    P = (1.0f - o3) * (KM(2, 1, 0) + KM(0, 1, 2)) + g3 * Fy;
-    D = (1.0f - o4) * (KM(2, 1, 0) - KM(0, 1, 2));
+    P = kp.om_c[3] * (KM(2, 1, 0) + KM(0, 1, 2)) + kp.g3 * Fy;
+    D = kp.om_c[4] * (KM(2, 1, 0) - KM(0, 1, 2));
     KM(2, 1, 0) = 0.5f * (P + D);
     KM(0, 1, 2) = 0.5f * (P - D);
-    P = (1.0f - o3) * (KM(2, 0, 1) + KM(0, 2, 1)) + g3 * Fz;
-    D = (1.0f - o4) * (KM(2, 0, 1) - KM(0, 2, 1));
+    P = kp.om_c[3] * (KM(2, 0, 1) + KM(0, 2, 1)) + kp.g3 * Fz;
+    D = kp.om_c[4] * (KM(2, 0, 1) - KM(0, 2, 1));
     KM(2, 0, 1) = 0.5f * (P + D);
     KM(0, 2, 1) = 0.5f * (P - D);
-    KM(1, 1, 1) *= (1.0f - o5);
+    KM(1, 1, 1) *= kp.om_c[5];
   }
   // fourth order (Eq. 24) with the approximate correction of Eq. 28
   {
     float Q220 = 0.0f, Q202 = 0.0f, Q022 = 0.0f;
     if (kp.q4) {
-      Q220 = (Qx + Qy) * cs2;
-      Q202 = (Qx + Qz) * cs2;
-      Q022 = (Qy + Qz) * cs2;
+      Q220 = (Qx + Qy) * (1.0f / 3.0f);
+      Q202 = (Qx + Qz) * (1.0f / 3.0f);
+      Q022 = (Qy + Qz) * (1.0f / 3.0f);
     }
     float a = KM(2, 2, 0), b = KM(2, 0, 2), c = KM(0, 2, 2);
-    float D1 = (1.0f - o6) * (a - 2.0f * b + c) + (1.0f - 0.5f * o6) * (Q220 - 2.0f * Q202 + Q022);
-    float D2 = (1.0f - o6) * (a + b - 2.0f * c) + (1.0f - 0.5f * o6) * (Q220 + Q202 - 2.0f * Q022);
-    float T = (1.0f - o7) * (a + b + c) + 3.0f * o7 * pm * cs2 +
-              (1.0f - 0.5f * o7) * (Q220 + Q202 + Q022);
+    float D1 = kp.om_c[6] * (a - 2.0f * b + c) + kp.om_h[6] * (Q220 - 2.0f * Q202 + Q022);
+    float D2 = kp.om_c[6] * (a + b - 2.0f * c) + kp.om_h[6] * (Q220 + Q202 - 2.0f * Q022);
+    float T = kp.om_c[7] * (a + b + c) + kp.om[7] * pm + kp.om_h[7] * (Q220 + Q202 + Q022);
     KM(2, 2, 0) = (T + D1 + D2) * (1.0f / 3.0f);
     KM(2, 0, 2) = (T - D1) * (1.0f / 3.0f);
     KM(0, 2, 2) = (T - D2) * (1.0f / 3.0f);
-    KM(2, 1, 1) *= (1.0f - o8);
-    KM(1, 2, 1) *= (1.0f - o8);
-    KM(1, 1, 2) *= (1.0f - o8);
+    KM(2, 1, 1) *= kp.om_c[8];
+    KM(1, 2, 1) *= kp.om_c[8];
+    KM(1, 1, 2) *= kp.om_c[8];
   }
   // fifth order (Eq. 25)
-  {
-    const float g5 = (1.0f - 0.5f * o9) * cs2 * cs2;
-    KM(1, 2, 2) = (1.0f - o9) * KM(1, 2, 2) + g5 * Fx;
-    KM(2, 1, 2) = (1.0f - o9) * KM(2, 1, 2) + g5 * Fy;
-    KM(2, 2, 1) = (1.0f - o9) * KM(2, 2, 1) + g5 * Fz;
-  }
+  KM(1, 2, 2) = kp.om_c[9] * KM(1, 2, 2) + kp.g5 * Fx;
+  KM(2, 1, 2) = kp.om_c[9] * KM(2, 1, 2) + kp.g5 * Fy;
+  KM(2, 2, 1) = kp.om_c[9] * KM(2, 2, 1) + kp.g5 * Fz;
   // sixth order (Eq. 26)
-  KM(2, 2, 2) = (1.0f - o10) * KM(2, 2, 2) + o10 * pm * cs2 * cs2;
+  KM(2, 2, 2) = kp.om_c[10] * KM(2, 2, 2) + kp.o10e * pm;
 }
 
 // Bulk chemical potential of the van der Waals EOS (bulk part of Eq. 32),

@@ -168,8 +168,9 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
 // ---------------------------------------------------------------------------
 // fused force / correction / collision / streaming
 // ---------------------------------------------------------------------------
-// column tile: one thread per (x, y); FUSED_MINB blocks per SM are requested
-// (32 x 4 with three blocks per SM measured fastest on GB300)
+// column tile: one thread per (x, y); the launch bounds ask for FUSED_MINB
+// blocks per SM (32 x 4 tiles measured fastest on GB300; registers and shared
+// memory admit four resident blocks)
 #ifndef LBM_FUSED_TX
 #define LBM_FUSED_TX 32
 #endif
