@@ -1,0 +1,173 @@
+"""Physical results the oracle must reproduce (Sec. III): the Laplace law of a
+stationary droplet, the neutral contact angle on a wall, and the shape of a
+droplet carried by a uniform flow.
+
+The 3-D runs of the paper are far too large for the FP64 oracle, so each
+check uses the same D3Q27 model on a quasi-2-D domain one node thick
+(periodic in that direction): every field is uniform along it, a sphere
+becomes a cylinder and the Laplace law reads Delta p = sigma / R.  Paper
+EOS (a = 9/392, b = 2/21, R = 1), T = 0.7 T_c, kappa = 0.02, all rates 1,
+initial tanh interfaces of width 5 (Eqs. 34-35).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import step as S
+from oracle import thermo as T
+from paper_2504_03819_gb300 import inputs as I
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+A392, B = 9.0 / 392.0, 2.0 / 21.0
+
+
+def setup(**kw):
+    eos = T.at_reduced_temperature(A392, B, 1.0, 0.7)
+    rl, rv = T.maxwell(eos)
+    p = S.Params(a=A392, b=B, R=1.0, T=eos.T, kappa=0.02, rho_l=rl, rho_v=rv, **kw)
+    return eos, p, rl, rv
+
+
+def cylinder(n, radius, rl, rv):
+    """Cylinder along z in an n x n x 1 domain, centred in x-y."""
+    return I.droplet(n, n, 1, radius, rl, rv, centre=((n - 1) / 2.0, (n - 1) / 2.0, 0.0))
+
+
+def test_laplace_law_cylinder():
+    """Sec. III B: at equilibrium the pressure jump across the interface of a
+    drop of radius R is sigma / R (cylinder) with sigma the flat-interface
+    value of Sec. III A (0.204, printed), and both bulk phases sit at one
+    chemical potential.  The equimolar radius R = 8.1 with an interface about
+    3 nodes wide leaves a curvature correction of a few percent, so the
+    product Delta p R is held to 7 % (measured 0.2137, +4.7 %); the bulk
+    chemical potentials of the two phases agree to 5 % of their common
+    Kelvin shift from coexistence (measured 1.7 %)."""
+    eos, p, rl, rv = setup()
+    n = 32
+    solid = torch.zeros(1, n, n, dtype=torch.bool)
+    f = S.initial_populations(torch.from_numpy(cylinder(n, 8.0, rl, rv)), None, solid, p)
+    f = S.run(f, solid, p, 500)
+    m = S.macroscopic(f, solid, p)
+    r = m["rho"][0]
+    rin, rout = float(r[n // 2, n // 2]), float(r[0, 0])
+    area = float(((r - rout) / (rin - rout)).sum())
+    req = math.sqrt(area / math.pi)
+    sigma = GOLD["surface_tension_flat_0p7Tc"]["sigma"]
+    dp = eos.p0(rin) - eos.p0(rout)
+    assert dp * req == pytest.approx(sigma, rel=0.07)
+    # one chemical potential: both bulk values moved by the same Kelvin shift
+    # (to 5 %; the centre and corner nodes still carry interface tails)
+    shift = eos.mu0(rin) - eos.mu0(rl)
+    assert abs(eos.mu0(rin) - eos.mu0(rout)) < 0.05 * abs(shift)
+    # and the drop is at rest: the residual (spurious) flow is small
+    assert float(m["u"].abs().max()) < 1e-4
+    # both phases moved off the flat coexistence densities the way the Kelvin
+    # effect does: the pressure jump raises both densities
+    assert rin > rl and rout > rv
+
+
+def contact_angle_2d(rho, mid, wall=0.5, zmin=2):
+    """Circle fit to the mid-density contour of a drop on the wall plane
+    z = wall (rows z >= zmin, points interpolated along x); the angle inside
+    the liquid."""
+    pts = []
+    nz, nx = rho.shape
+    for z in range(zmin, nz - 2):
+        row = rho[z]
+        for x in range(nx - 1):
+            if (row[x] - mid) * (row[x + 1] - mid) < 0:
+                pts.append((x + (mid - row[x]) / (row[x + 1] - row[x]), float(z)))
+    P = np.array(pts)
+    A = np.c_[2 * P, np.ones(len(P))]
+    cx, cz, c = np.linalg.lstsq(A, (P ** 2).sum(1), rcond=None)[0]
+    rad = math.sqrt(c + cx * cx + cz * cz)
+    return math.degrees(math.acos(max(-1.0, min(1.0, -(cz - wall) / rad))))
+
+
+def test_neutral_wetting_contact_angle():
+    """Sec. III C: with the surface density set to the fluid-weighted average
+    (Eq. 37, no contact-line modification) and the surface chemical potential
+    of Eq. 36, a drop keeps neutral wetting, 90 degrees (the paper prints
+    89.9 for its 3-D drop).  A half-cylinder on the bottom wall of a
+    40 x 1 x 20 domain (solid planes z = 0 and 19), angle from a circle fit
+    to the mid-density contour."""
+    eos, p, rl, rv = setup(wetting_mode=0)
+    nx, nz = 40, 20
+    mask = I.wall_mask(nx, 1, nz, planes=(0, nz - 1))
+    solid = torch.from_numpy(mask.astype(bool))
+    rho0 = I.sessile_droplet(nx, 1, nz, 8.0, rl, rv, wall_z=0.5)
+    f = S.initial_populations(torch.from_numpy(rho0), None, solid, p)
+    f = S.run(f, solid, p, 500)
+    m = S.macroscopic(f, solid, p)
+    theta = contact_angle_2d(m["rho"][:, 0, :].numpy(), 0.5 * (rl + rv))
+    assert theta == pytest.approx(GOLD["contact_angles"]["neutral"], abs=1.5)
+    assert float(m["mass"]) == pytest.approx(float(rho0[~mask.astype(bool)].sum()), rel=1e-12)
+
+
+def test_translated_cylinder_keeps_its_shape(monkeypatch):
+    """Sec. III B: with the third- and fourth-order corrections the model is
+    Galilean invariant, so a drop carried by a uniform flow keeps its shape
+    (models without them deform it).  An equilibrated cylinder is given a
+    uniform velocity U = 0.1 and run for one period of the box (320 steps);
+    the droplet position drifts a little (momentum is conserved only to the
+    lattice force balance), so shapes are compared about their own centroid:
+    the density field re-centred by a Fourier shift matches the stationary
+    one to 8 % of the density contrast and the drop stays round to 3 %
+    (measured 5.7 % and 2 %).  The same run without the corrections (Q = 0,
+    hence no fourth-order term either) goes non-finite."""
+    err, asp = _translate(1.0, monkeypatch)
+    assert err < 0.08
+    assert asp == pytest.approx(1.0, abs=0.03)
+    err0, _ = _translate(0.0, monkeypatch)
+    assert not err0 < 3 * 0.08
+
+
+def _translate(q_scale, monkeypatch):
+    eos, p, rl, rv = setup()
+    n = 32
+    solid = torch.zeros(1, n, n, dtype=torch.bool)
+    f = S.initial_populations(torch.from_numpy(cylinder(n, 8.0, rl, rv)), None, solid, p)
+    rest = S.macroscopic(S.run(f, solid, p, 300), solid, p)["rho"][0]
+    u0 = torch.zeros(3, 1, n, n, dtype=torch.float64)
+    u0[0] = 0.1
+    f = S.initial_populations(rest.view(1, n, n), u0, solid, p)
+    orig = S.fields
+
+    def scaled(ff, ss, pp):
+        d = orig(ff, ss, pp)
+        d["Q"] = d["Q"] * q_scale
+        return d
+
+    monkeypatch.setattr(S, "fields", scaled)
+    moved = S.macroscopic(S.run(f, solid, p, 320), solid, p)["rho"][0]
+    monkeypatch.setattr(S, "fields", orig)
+    if not torch.isfinite(moved).all():
+        return math.inf, math.inf
+
+    def centroid(r, axis):
+        ang = 2 * math.pi * torch.arange(n, dtype=torch.float64) / n
+        w = (r - rv).sum(dim=1 - axis)
+        return math.atan2(float((w * torch.sin(ang)).sum()), float((w * torch.cos(ang)).sum())) / (2 * math.pi) * n
+
+    dx = centroid(moved, 1) - centroid(rest, 1)
+    dy = centroid(moved, 0) - centroid(rest, 0)
+    kx = torch.fft.fftfreq(n, dtype=torch.float64).view(1, n)
+    ky = torch.fft.fftfreq(n, dtype=torch.float64).view(n, 1)
+    back = torch.fft.ifft2(torch.fft.fft2(moved) * torch.exp(2j * math.pi * (kx * dx + ky * dy))).real
+    err = float((back - rest).abs().max()) / (rl - rv)
+
+    def aspect(r):
+        w = (r - rv).clamp_min(0)
+        cx, cy = centroid(r, 1), centroid(r, 0)
+        x = torch.arange(n, dtype=torch.float64)
+        ddx = torch.remainder(x - cx + n / 2, n) - n / 2
+        ddy = torch.remainder(x - cy + n / 2, n) - n / 2
+        ixx = float((w * ddx.view(1, n) ** 2).sum())
+        iyy = float((w * ddy.view(n, 1) ** 2).sum())
+        return ixx / iyy
+
+    return err, aspect(moved)
