@@ -28,8 +28,14 @@ Readings where the paper is silent (each is listed in the design notes):
   * on solid nodes u = 0, hence the flux (p_m - rho/3) u = 0 there;
   * solid nodes with no fluid neighbour get rho = mu = 0 (never read);
   * the contact-line limiter acts only on densities modified by Eq. 38;
-  * halfway bounce-back for walls at rest: a population whose source node
-    x - c_i is solid is the opposite post-collision population of x itself.
+  * halfway bounce-back: a population whose source node x - c_i is solid is
+    the opposite post-collision population of x itself; for a wall moving
+    with velocity U_w (Sec. III B uses moving walls, with no formula) it
+    gains f^eq_i(U_w) - f^eq_-i(U_w), the part of the generalized equilibrium
+    (Eq. 13) odd in the velocity, to first order in U_w, at the rho and p_m of
+    the fluid node x:  2 w_i (c_i . U_w) / c_s^2 * A with A = p_m / c_s^2 for
+    edge and corner velocities and A = p_m / c_s^2 + (9/4)(rho - p_m / c_s^2)
+    for face velocities (for p_m = rho c_s^2 the usual A = rho).
 """
 from __future__ import annotations
 
@@ -55,6 +61,8 @@ class Params:
     nu <= 0 keeps omega_1 = omega[1].
     wetting_mode: 0 neutral (rho_s = rho_ave), 1 rho_s = phi rho_ave,
     2 rho_s = rho_ave - delta_rho (Eq. 38); wetting_value is phi or delta_rho.
+    wall_u: None (walls at rest) or a (3, nz, ny, nx) float64 tensor whose
+    values on solid nodes are the wall velocities (fluid entries unused).
     kappa, omega and wetting_value may be 0-d / 1-d float64 tensors with
     requires_grad for gradient checks.
     """
@@ -70,6 +78,7 @@ class Params:
     wetting_value: object = 1.0
     rho_l: float = 0.0
     rho_v: float = 0.0
+    wall_u: object = None
 
     def omega_t(self) -> torch.Tensor:
         return torch.as_tensor(self.omega, dtype=DT)
@@ -293,15 +302,33 @@ def collide(f: torch.Tensor, solid: torch.Tensor, fl: dict, p: Params) -> torch.
 # ---------------------------------------------------------------------------
 # Step 8: streaming with halfway bounce-back (Eq. 10, Sec. III C)
 # ---------------------------------------------------------------------------
-def stream(fs: torch.Tensor, solid: torch.Tensor) -> torch.Tensor:
-    """f_i(x, t+1) = f*_i(x - c_i); if x - c_i is solid, f_i(x, t+1) = f*_{-i}(x)."""
+def wall_odd_equilibrium(i: int, rho: torch.Tensor, pm: torch.Tensor, uw: torch.Tensor) -> torch.Tensor:
+    """f^eq_i - f^eq_-i of the generalized equilibrium (Eq. 13) at velocity
+    uw, to first order in uw: 2 w_i (c_i . uw) / c_s^2 * A, A = p_m / c_s^2
+    (|c_i|^2 = 2, 3) or p_m / c_s^2 + (9/4)(rho - p_m / c_s^2) (|c_i|^2 = 1)."""
+    cx, cy, cz = (int(v) for v in C[i])
+    a = pm / CS2
+    if cx * cx + cy * cy + cz * cz == 1:
+        a = a + 2.25 * (rho - pm / CS2)
+    return 2.0 * W[i] * (cx * uw[0] + cy * uw[1] + cz * uw[2]) / CS2 * a
+
+
+def stream(fs: torch.Tensor, solid: torch.Tensor, rho: torch.Tensor | None = None,
+           pm: torch.Tensor | None = None, wall_u: torch.Tensor | None = None) -> torch.Tensor:
+    """f_i(x, t+1) = f*_i(x - c_i); if x - c_i is solid, f_i(x, t+1) =
+    f*_{-i}(x) + [f^eq_i - f^eq_-i](rho(x), p_m(x), U_w(x - c_i)) (the last
+    term only for moving walls, wall_u given)."""
     fluid = ~solid
     out = []
     for i in range(27):
         cx, cy, cz = (int(v) for v in C[i])
         pulled = torch.roll(fs[i], shifts=(cz, cy, cx), dims=(0, 1, 2))
         src_solid = torch.roll(solid, shifts=(cz, cy, cx), dims=(0, 1, 2))
-        v = torch.where(src_solid, fs[OPP[i]], pulled)
+        back = fs[OPP[i]]
+        if wall_u is not None:
+            uw = torch.roll(wall_u, shifts=(cz, cy, cx), dims=(1, 2, 3))
+            back = back + wall_odd_equilibrium(i, rho, pm, uw)
+        v = torch.where(src_solid, back, pulled)
         out.append(torch.where(fluid, v, torch.zeros_like(v)))
     return torch.stack(out)
 
@@ -309,7 +336,7 @@ def stream(fs: torch.Tensor, solid: torch.Tensor) -> torch.Tensor:
 def step(f: torch.Tensor, solid: torch.Tensor, p: Params) -> torch.Tensor:
     """One full time step f(t) -> f(t+1)."""
     fl = fields(f, solid, p)
-    return stream(collide(f, solid, fl, p), solid)
+    return stream(collide(f, solid, fl, p), solid, fl["rho"], fl["pm"], p.wall_u)
 
 
 def run(f: torch.Tensor, solid: torch.Tensor, p: Params, n: int) -> torch.Tensor:

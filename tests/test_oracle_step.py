@@ -345,3 +345,38 @@ def test_third_order_correction_keeps_translating_interface(monkeypatch):
     assert ok < 0.1
     assert _translated_interface_error(0.0, monkeypatch) > 10 * ok
     assert _translated_interface_error(-1.0, monkeypatch) > 10 * ok
+
+
+def test_moving_wall_couette_profile():
+    """Moving halfway wall (Sec. III B drives its Galilean test with moving
+    walls): a uniform-density channel (mu uniform, so F = Q = 0) between a wall
+    at rest (z = 0) and a wall moving at U along x (z = 11) reaches the exact
+    linear Couette profile u_x(z) = U (z - 1/2) / 10 between the halfway wall
+    planes, mass is conserved, and no normal flow appears.  A wall term with
+    the standard coefficient rho instead of the generalized equilibrium's odd
+    part (p_m != rho c_s^2 here) gives a profile about 1.5x too steep."""
+    p0, rl, rv = params()
+    nz, U = 12, 0.01
+    solid = torch.from_numpy(I.wall_mask(1, 1, nz, planes=(0, nz - 1)).astype(bool))
+    wu = torch.zeros(3, nz, 1, 1, dtype=DT)
+    wu[0, nz - 1] = U
+    p = S.Params(**{**p0.__dict__, "wall_u": wu})
+    f = S.initial_populations(torch.full((nz, 1, 1), 2.0, dtype=DT), None, solid, p)
+    f = S.run(f, solid, p, 1500)
+    m = S.macroscopic(f, solid, p)
+    ux = m["u"][0, 1:nz - 1, 0, 0]
+    exact = U * (torch.arange(1, nz - 1, dtype=DT) - 0.5) / (nz - 2)
+    assert float((ux - exact).abs().max()) < 1e-5 * U
+    assert float(m["u"][2].abs().max()) < 1e-12
+    assert float(m["mass"]) == pytest.approx(2.0 * (nz - 2), rel=1e-12)
+
+
+def test_moving_wall_term_is_the_equilibrium_odd_part():
+    """The moving-wall term equals f^eq_i(U) - f^eq_-i(U) of Eq. 13 to first
+    order in U, for any rho and p_m."""
+    for rho, pm in ((2.0, 0.4349), (6.0, 0.33), (1.0, 0.9)):
+        r, m_ = torch.tensor(rho, dtype=DT), torch.tensor(pm, dtype=DT)
+        u = torch.tensor([1e-6, -4e-7, 3e-7], dtype=DT)
+        d = L.f_eq_phase_space(r, u, m_).reshape(27) - L.f_eq_phase_space(r, -u, m_).reshape(27)
+        got = torch.stack([S.wall_odd_equilibrium(i, r, m_, u) for i in range(27)])
+        assert float((got - d).abs().max()) < 1e-9 * float(d.abs().max())
