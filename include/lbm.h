@@ -137,6 +137,22 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage,
 int lbm_set_params(lbm_ctx *ctx, const lbm_params *params);
 
 /*
+ * Moving walls (Sec. III B drives its Galilean test with walls moving at a
+ * constant velocity; the paper gives no boundary formula).  wall_u: device,
+ * 3*N floats SoA (x, y, z planes), the velocity of each solid node (values on
+ * fluid nodes are ignored), or NULL for walls at rest (the default).  A
+ * population bounced back from a solid node moving with U gains the part of
+ * the generalized equilibrium (Eq. 13) odd in the velocity, at U to first
+ * order and at the rho and p_m of the fluid node: 2 w_i (c_i . U) / c_s^2 * A
+ * with A = p_m / c_s^2 (edge and corner velocities) or p_m / c_s^2 +
+ * (9/4)(rho - p_m / c_s^2) (face velocities).  The library keeps the pointer
+ * (caller-owned: it must stay valid while steps and adjoint steps that use it
+ * are enqueued).  Applies to lbm_step, lbm_adjoint_step and
+ * lbm_adjoint_segment.  LBM_ERR_STATE for a domain without walls.
+ */
+int lbm_set_wall_velocity(lbm_ctx *ctx, const float *wall_u);
+
+/*
  * Initial state: populations at the equilibrium whose central moments are
  * those of Eq. 20 about u0, with rho = rho0 and p_m = (1 + mu(rho0))/3
  * (mu from Eqs. 2, 32 and the wetting values of Eqs. 36-38 on solid nodes).

@@ -31,6 +31,7 @@ SIGNATURES = {
     "lbm_init_domain": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                   C.c_void_p, C.c_size_t, C.c_void_p]),
     "lbm_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_set_wall_velocity": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_sync_status": (C.c_int, [C.c_void_p]),
@@ -221,6 +222,18 @@ class Domain:
         self._params_c = p.to_c(self.storage)
         self.params = p
         self._check(self.lib.lbm_set_params(self.ctx, C.byref(self._params_c)), "lbm_set_params")
+
+    def set_wall_velocity(self, wall_u=None):
+        """Velocities of the solid nodes, shape (3, nz, ny, nx) (values on
+        fluid nodes unused), or None for walls at rest.  The device copy is
+        kept alive by the domain."""
+        if wall_u is None:
+            self._wall_u = None
+            ptr = None
+        else:
+            self._wall_u = self._dev(wall_u, (3, self.nz, self.ny, self.nx))
+            ptr = _ptr(self._wall_u)
+        self._check(self.lib.lbm_set_wall_velocity(self.ctx, ptr), "lbm_set_wall_velocity")
 
     def set_state(self, rho0, u0=None):
         shp = (self.nz, self.ny, self.nx)

@@ -369,7 +369,8 @@ template <typename T>
 __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(const T *__restrict__ fstate, const float *__restrict__ sb,
                                                      const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
                                                      const float *__restrict__ lam_next, float *__restrict__ lam_t,
-                                                     Fields d, AdjFields a, double *__restrict__ partial, KParams kp) {
+                                                     Fields d, AdjFields a, const float *__restrict__ wall_u,
+                                                     double *__restrict__ partial, KParams kp) {
   const Site st = site_of(kp);
   const int n = st.n;
   float pg[11];  // dJ/d omega_0..omega_10 of this node
@@ -403,6 +404,20 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(con
         }
         lam[q] = ((solid >> q) & 1u) ? lam_next[(size_t)(26 - q) * N + n]
                                      : lam_next[q * N + st.at(cx_of(q), cy_of(q), cz_of(q))];
+      }
+      // moving walls: the bounced population carries -wall_odd(q, rho, p_m,
+      // U(x + c_q)); its rho and p_m derivatives
+      float lr_wall = 0.0f, lpm_wall = 0.0f;
+      if (wall_u && solid) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+          if (q == 13 || !((solid >> q) & 1u)) continue;
+          const int b = st.at(cx_of(q), cy_of(q), cz_of(q));
+          const float cu = cx_of(q) * wall_u[b] + cy_of(q) * wall_u[N + b] + cz_of(q) * wall_u[2 * N + b];
+          const float g = -6.0f * weight_of(q) * cu * lam[q];
+          lr_wall += g * wall_coef_rho(q);
+          lpm_wall += g * wall_coef_pm(q);
+        }
       }
       const float ux = d.u[n], uy = d.u[N + n], uz = d.u[2 * N + n];
       const float Fx = d.F[n], Fy = d.F[N + n], Fz = d.F[2 * N + n];
@@ -439,8 +454,8 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 2) k_adj_collide(con
       a.Q[n] = lQx;
       a.Q[N + n] = lQy;
       a.Q[2 * N + n] = lQz;
-      a.pm[n] = lpm;
-      a.rho[n] = 0.0f;  // direct density adjoint: none in a step
+      a.pm[n] = lpm + lpm_wall;
+      a.rho[n] = lr_wall;  // direct density adjoint: only from moving walls
       if (kp.nu > 0.0f) {
         a.om1[n] = lom1;
       } else {
@@ -961,10 +976,10 @@ void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_nex
   }
   if (ctx->storage == LBM_F16)
     k_adj_collide<__half><<<g4, b4, 0, s>>>((const __half *)f_state, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d,
-                                           ctx->adj, R.collide, kp);
+                                           ctx->adj, ctx->mask ? ctx->wall_u : nullptr, R.collide, kp);
   else
     k_adj_collide<float><<<g4, b4, 0, s>>>((const float *)f_state, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d,
-                                          ctx->adj, R.collide, kp);
+                                          ctx->adj, ctx->mask ? ctx->wall_u : nullptr, R.collide, kp);
   k_adj_fields<<<g8, b8, 0, s>>>(ctx->mask, d, ctx->adj, kp);
   ctx->launches += 2;
   const float *lmu = adj_mu(ctx);

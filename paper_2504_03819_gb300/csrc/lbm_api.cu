@@ -256,6 +256,13 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
   return LBM_OK;
 }
 
+int lbm_set_wall_velocity(lbm_ctx *ctx, const float *wall_u) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (wall_u && !ctx->mask) return fail(ctx, LBM_ERR_STATE, "wall velocities need a domain with a solid mask");
+  ctx->wall_u = wall_u;
+  return LBM_OK;
+}
+
 int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0) {
   if (!ctx) return LBM_ERR_ARG;
   if (!ctx->have_params) return fail(ctx, LBM_ERR_STATE, "lbm_set_params must come first");

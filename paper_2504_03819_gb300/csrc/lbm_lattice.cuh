@@ -225,6 +225,23 @@ __device__ __forceinline__ float mu0_vdw(float r, const KParams &kp) {
   return (liq ? kp.ref_dmu[1] : kp.ref_dmu[0]) + kp.RT * t - 2.0f * kp.a * d;
 }
 
+// Moving halfway wall: f^eq_q - f^eq_-q of the generalized equilibrium
+// (Eq. 13) at the wall velocity U to first order, at the fluid node's rho and
+// p_m: 2 w_q (c_q . U) / c_s^2 * A with A = p_m / c_s^2 for edge and corner
+// velocities and A = p_m / c_s^2 + (9/4)(rho - p_m / c_s^2) for faces.  Sec.
+// III B uses moving walls without giving the term; for p_m = rho c_s^2 it is
+// the usual 2 w_q rho (c_q . U) / c_s^2.
+__device__ __forceinline__ float wall_coef_rho(int q) {  // dA/drho
+  return (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 1 ? 2.25f : 0.0f;
+}
+__device__ __forceinline__ float wall_coef_pm(int q) {  // dA/dp_m
+  return (cx_of(q) * cx_of(q) + cy_of(q) * cy_of(q) + cz_of(q) * cz_of(q)) == 1 ? 3.0f - 6.75f : 3.0f;
+}
+__device__ __forceinline__ float wall_odd(int q, float rho, float pm, float ux, float uy, float uz) {
+  const float cu = cx_of(q) * ux + cy_of(q) * uy + cz_of(q) * uz;
+  return 6.0f * weight_of(q) * cu * (wall_coef_pm(q) * pm + wall_coef_rho(q) * rho);
+}
+
 // p_m = (1 + mu)/3 from mu' = mu - mu_ref.
 __device__ __forceinline__ float pm_of(float mup, const KParams &kp) {
   return fmaf(mup, 1.0f / 3.0f, kp.pm_ref);

@@ -221,7 +221,8 @@ template <typename T, bool MASK, bool TMA>
 __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
-            float *__restrict__ sb, int *__restrict__ status, float *__restrict__ cap, KParams kp, int TZ,
+            float *__restrict__ sb, int *__restrict__ status, float *__restrict__ cap,
+            const float *__restrict__ wall_u, KParams kp, int TZ,
             const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
@@ -501,6 +502,10 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       const int hk = c1 + cx + cy * H1X;
       if (MASK && S.solid[r4(z + cz)][hk]) {
         if (rest) sh = shift_rest(q, r_own, c_own);
+        if (wall_u) {  // moving wall: the velocity of the solid node x + c_q
+          const int b = n + ox[cx + 1] + oy[cy + 1] + oz[cz + 1];
+          sh += wall_odd(q, r_own, pm, wall_u[b], wall_u[N + b], wall_u[2 * N + b]);
+        }
         store_pop<T>(fout + (size_t)(26 - q) * N + n, f[q] - sh);
       } else {
         if (rest) sh = S.shift[r3(z + cz)][cx * cx + cy * cy + cz * cz][hk];
@@ -641,7 +646,8 @@ void launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map)
   const int tz = z_chunk(xyb, kp.nz, resident_slots<k_fused<T, MASK, TMA>>(NT, sm), 2);
   const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
   k_fused<T, MASK, TMA><<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j, d.mu, d.sb,
-                                                       ctx->status, ctx->capture, kp, tz, map);
+                                                       ctx->status, ctx->capture, MASK ? ctx->wall_u : nullptr, kp,
+                                                       tz, map);
 }
 
 template <typename T>
