@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
 // fused force / correction / collision / streaming
 // ---------------------------------------------------------------------------
 // column tile: one thread per (x, y); the launch bounds ask for FUSED_MINB
-// blocks per SM (32 x 4 tiles measured fastest on GB300; registers and shared
-// memory admit four resident blocks)
+// blocks per SM (32 x 4 tiles measured fastest on GB300; four blocks fill
+// the shared memory and cap the registers at 128, with no spills)
 #ifndef LBM_FUSED_TX
 #define LBM_FUSED_TX 32
 #endif
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
 #define LBM_FUSED_TY 4
 #endif
 #ifndef LBM_FUSED_MINB
-#define LBM_FUSED_MINB 3
+#define LBM_FUSED_MINB 4
 #endif
 constexpr int TX = LBM_FUSED_TX, TY = LBM_FUSED_TY;
 constexpr int NT = TX * TY;
@@ -216,8 +216,10 @@ template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return _
 // MASK: the domain has solid nodes (bounce-back and solid checks compiled
 // in).  TMA: the populations of each plane arrive in shared memory by one
 // tensor copy issued a plane ahead (tmap describes fin as [27][nz][ny][nx]);
-// otherwise each thread loads its node's populations directly.
-template <typename T, bool MASK, bool TMA>
+// otherwise each thread loads its node's populations directly.  WALLV: the
+// walls move (wall_u holds the solid nodes' velocities); compiled out of the
+// resting-wall instantiations, whose registers it would raise.
+template <typename T, bool MASK, bool TMA, bool WALLV>
 __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       const int hk = c1 + cx + cy * H1X;
       if (MASK && S.solid[r4(z + cz)][hk]) {
         if (rest) sh = shift_rest(q, r_own, c_own);
-        if (wall_u) {  // moving wall: the velocity of the solid node x + c_q
+        if (WALLV) {  // moving wall: the velocity of the solid node x + c_q
           const int b = n + ox[cx + 1] + oy[cy + 1] + oz[cz + 1];
           sh += wall_odd(q, r_own, pm, wall_u[b], wall_u[N + b], wall_u[2 * N + b]);
         }
@@ -636,18 +638,18 @@ const CUtensorMap *population_tmap(lbm_ctx *ctx, const void *p) {
   return e.ok ? &e.map : nullptr;
 }
 
-template <typename T, bool MASK, bool TMA>
+template <typename T, bool MASK, bool TMA, bool WALLV>
 void launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
   const KParams &kp = ctx->kp;
   const Fields &d = ctx->fld;
   constexpr size_t sm = fused_smem_size<T>(TMA);
-  ensure_smem<k_fused<T, MASK, TMA>>(sm);
+  ensure_smem<k_fused<T, MASK, TMA, WALLV>>(sm);
   const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
-  const int tz = z_chunk(xyb, kp.nz, resident_slots<k_fused<T, MASK, TMA>>(NT, sm), 2);
+  const int tz = z_chunk(xyb, kp.nz, resident_slots<k_fused<T, MASK, TMA, WALLV>>(NT, sm), 2);
   const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
-  k_fused<T, MASK, TMA><<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j, d.mu, d.sb,
-                                                       ctx->status, ctx->capture, MASK ? ctx->wall_u : nullptr, kp,
-                                                       tz, map);
+  k_fused<T, MASK, TMA, WALLV><<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j,
+                                                              d.mu, d.sb, ctx->status, ctx->capture,
+                                                              WALLV ? ctx->wall_u : nullptr, kp, tz, map);
 }
 
 template <typename T>
@@ -655,16 +657,22 @@ void launch_fused(lbm_ctx *ctx, const void *fin_v, void *fout_v) {
   const T *fin = static_cast<const T *>(fin_v);
   T *fout = static_cast<T *>(fout_v);
   const CUtensorMap *map = population_tmap(ctx, fin_v);
+  const bool moving = ctx->mask && ctx->wall_u;
   if (map) {
-    if (ctx->mask)
-      launch_fused_k<T, true, true>(ctx, fin, fout, *map);
+    if (moving)
+      launch_fused_k<T, true, true, true>(ctx, fin, fout, *map);
+    else if (ctx->mask)
+      launch_fused_k<T, true, true, false>(ctx, fin, fout, *map);
     else
-      launch_fused_k<T, false, true>(ctx, fin, fout, *map);
+      launch_fused_k<T, false, true, false>(ctx, fin, fout, *map);
   } else {
     // rows that a tensor copy cannot describe: per-thread loads, the mask
     // checks compiled in (an all-fluid domain has an all-zero solid plane)
     static const CUtensorMap unused{};
-    launch_fused_k<T, true, false>(ctx, fin, fout, unused);
+    if (moving)
+      launch_fused_k<T, true, false, true>(ctx, fin, fout, unused);
+    else
+      launch_fused_k<T, true, false, false>(ctx, fin, fout, unused);
   }
 }
 
