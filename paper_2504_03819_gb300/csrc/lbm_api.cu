@@ -19,7 +19,7 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 // Workspace layout (each region 256-byte aligned):
 //   f[0], f[1]      27 N elements of the storage type each
-//   fields          rho N, j 3N, mu N, u 3N, F 3N, phi 3N, Q 3N, sb 2N floats
+//   fields          rho N, j 3N, mu N, u 3N, F 3N, phi 3N, Q 3N, sb 2N, mu0 N floats
 //   boundary list   N ints
 //   neighbours      N uint32 solid-neighbour bitmasks, N floats of inverse
 //                   fluid-weight sums, N/256 + 2 ints of compaction counts
@@ -40,7 +40,7 @@ bool layout(int nx, int ny, int nz, int storage, Layout *L) {
   size_t off = 0;
   L->f0 = off; off = align_up(off + 27 * (size_t)N * elem);
   L->f1 = off; off = align_up(off + 27 * (size_t)N * elem);
-  L->fields = off; off = align_up(off + 19 * (size_t)N * sizeof(float));
+  L->fields = off; off = align_up(off + 20 * (size_t)N * sizeof(float));
   L->bnd = off; off = align_up(off + (size_t)N * sizeof(int));
   L->nbr = off; off = align_up(off + (size_t)N * sizeof(uint32_t));
   L->inv_den = off; off = align_up(off + (size_t)N * sizeof(float));
@@ -156,6 +156,7 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
   ctx->fld.phi = fl + 11 * N;
   ctx->fld.Q = fl + 14 * N;
   ctx->fld.sb = fl + 17 * N;
+  ctx->fld.mu0 = fl + 19 * N;
   ctx->bnd = (int *)(base + L.bnd);
   ctx->nbr = (uint32_t *)(base + L.nbr);
   ctx->inv_den = (float *)(base + L.inv_den);
@@ -177,7 +178,7 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
   ctx->kp.nz = nz;
   ctx->kp.N = ctx->N;
   cudaGetLastError();
-  cudaMemsetAsync(ctx->fld.rho, 0, 19 * N * sizeof(float), ctx->stream);
+  cudaMemsetAsync(ctx->fld.rho, 0, 20 * N * sizeof(float), ctx->stream);
   // solid-node population slots are never written by the step: start them at 0
   cudaMemsetAsync(ctx->f[0], 0, L.f1 - L.f0, ctx->stream);
   cudaMemsetAsync(ctx->f[1], 0, L.f1 - L.f0, ctx->stream);

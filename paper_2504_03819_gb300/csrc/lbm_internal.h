@@ -46,6 +46,8 @@ struct Fields {
   float *phi;  // 3N    (p_m - rho/3) u
   float *Q;    // 3N    Q_200, Q_020, Q_002
   float *sb;   // 2N    shift bases of LBM_SHIFT_REST: rho, then p_m - rho/3
+  float *mu0;  // N     mu0(rho) - mu_ref of the fluid nodes, handed from the
+               //       moments kernel to the chemical-potential kernel
 };
 
 // Adjoint scratch (reused between the stages of one adjoint step).

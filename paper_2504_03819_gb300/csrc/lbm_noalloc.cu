@@ -9,12 +9,12 @@
 namespace {
 
 // Scratch layout for N <= LBM_NOALLOC_MAX_NODES nodes, mirroring the field
-// part of the workspace: 19 floats per node (rho, j, mu', u, F, phi, Q, shift
-// bases), the boundary list (one int per node), the solid-neighbour bitmasks
+// part of the workspace: 20 floats per node (rho, j, mu', u, F, phi, Q, shift
+// bases, mu0), the boundary list (one int per node), the solid-neighbour bitmasks
 // and inverse fluid-weight sums (one word each per node), the compaction
 // counts (one int per 256 nodes) and two status ints.
 constexpr size_t kMax = LBM_NOALLOC_MAX_NODES;
-constexpr size_t kFieldBytes = 19 * kMax * sizeof(float);
+constexpr size_t kFieldBytes = 20 * kMax * sizeof(float);
 constexpr size_t kBndOff = kFieldBytes;
 constexpr size_t kNbrOff = kBndOff + kMax * sizeof(int);
 constexpr size_t kInvDenOff = kNbrOff + kMax * sizeof(uint32_t);
@@ -80,6 +80,7 @@ extern "C" int lbm_step_noalloc(const float *f_in, float *f_out, const uint8_t *
   ctx.fld.phi = fl + 11 * n;
   ctx.fld.Q = fl + 14 * n;
   ctx.fld.sb = fl + 17 * n;
+  ctx.fld.mu0 = fl + 19 * n;
   ctx.bnd = (int *)((char *)base + kBndOff);
   ctx.nbr = (uint32_t *)((char *)base + kNbrOff);
   ctx.inv_den = (float *)((char *)base + kInvDenOff);
@@ -100,7 +101,7 @@ extern "C" int lbm_step_noalloc(const float *f_in, float *f_out, const uint8_t *
 
   cudaGetLastError();
   // the array keeps the previous call's contents: clear what must start at 0
-  cudaMemsetAsync(base, 0, 19 * n * sizeof(float), ctx.stream);
+  cudaMemsetAsync(base, 0, 20 * n * sizeof(float), ctx.stream);
   cudaMemsetAsync(ctx.status, 0, 2 * sizeof(int), ctx.stream);
   cudaMemsetAsync(f_out, 0, 27 * n * sizeof(float), ctx.stream);  // solid-node slots stay 0
   if (solid_mask) {

@@ -1,6 +1,7 @@
 // Fused time step (Sec. II B): three kernels per step instead of seven.
 //
-//   k_moments_v   rho, j from the populations (Eq. 11) + status check
+//   k_moments_v   rho, j from the populations (Eq. 11), mu0(rho) - mu_ref,
+//                 status check
 //   k_mu_z        mu' = mu0(rho) - mu_ref - kappa lap rho on fluid nodes
 //                 (Eqs. 2, 32), marching in z with the rho planes in shared
 //                 memory and the separable 27-point Laplacian
@@ -33,7 +34,8 @@ __device__ __forceinline__ constexpr float w1(int c) { return c == 0 ? 2.0f / 3.
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments_v(const T *__restrict__ f, const uint8_t *__restrict__ mask,
                                                    const float *__restrict__ sb, float *__restrict__ rho,
-                                                   float *__restrict__ j, int *__restrict__ status, KParams kp) {
+                                                   float *__restrict__ j, float *__restrict__ mu0,
+                                                   int *__restrict__ status, KParams kp) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   bool bad_nf = false, bad_dom = false;
   if (n < kp.N && !(mask && mask[n])) {
@@ -58,8 +60,61 @@ __global__ void __launch_bounds__(256) k_moments_v(const T *__restrict__ f, cons
     j[n] = sx;
     j[N + n] = sy;
     j[2 * N + n] = sz;
+    // the bulk chemical potential here, where the issue slots are idle (this
+    // kernel waits on HBM), rather than in the issue-bound stencil kernel
+    mu0[n] = mu0_vdw(r, kp);
     bad_nf = !(isfinite(r) && isfinite(sx) && isfinite(sy) && isfinite(sz));
     bad_dom = !bad_nf && !(r > 0.0f && kp.b * r < 1.0f);
+  }
+  const unsigned nf = __ballot_sync(0xffffffffu, bad_nf), dm = __ballot_sync(0xffffffffu, bad_dom);
+  if ((threadIdx.x & 31) == 0) {
+    if (nf) atomicOr(status, STATUS_NONFINITE);
+    if (dm) atomicOr(status, STATUS_DOMAIN);
+  }
+}
+
+// FP16 storage: two neighbouring nodes per thread through __half2 loads (N
+// even, so every pair is 4-byte aligned); the same sums per node
+__global__ void __launch_bounds__(256) k_moments_h2(const __half *__restrict__ f, const uint8_t *__restrict__ mask,
+                                                    const float *__restrict__ sb, float *__restrict__ rho,
+                                                    float *__restrict__ j, float *__restrict__ mu0,
+                                                    int *__restrict__ status, KParams kp) {
+  const int n0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  bool bad_nf = false, bad_dom = false;
+  if (n0 < kp.N) {
+    const size_t N = (size_t)kp.N;
+    float v0[27], v1[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const float2 p = __half22float2(__ldg(reinterpret_cast<const __half2 *>(f + q * N + n0)));
+      v0[q] = p.x;
+      v1[q] = p.y;
+    }
+    auto finish = [&](const float (&v)[27], int n) {
+      if (mask && mask[n]) return;
+      float s = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 27; ++q) s += v[q];
+#pragma unroll
+      for (int q = 0; q < 27; q += 3) sx += v[q + 2] - v[q];
+#pragma unroll
+      for (int g = 0; g < 3; ++g)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sy += v[a + 6 + 9 * g] - v[a + 9 * g];
+#pragma unroll
+      for (int p = 0; p < 9; ++p) sz += v[p + 18] - v[p];
+      const float r = s + (kp.shift_mode == LBM_SHIFT_REST ? sb[n] : kp.rho_shift);
+      rho[n] = r;
+      j[n] = sx;
+      j[N + n] = sy;
+      j[2 * N + n] = sz;
+      mu0[n] = mu0_vdw(r, kp);
+      const bool nf = !(isfinite(r) && isfinite(sx) && isfinite(sy) && isfinite(sz));
+      bad_nf |= nf;
+      bad_dom |= !nf && !(r > 0.0f && kp.b * r < 1.0f);
+    };
+    finish(v0, n0);
+    finish(v1, n0 + 1);
   }
   const unsigned nf = __ballot_sync(0xffffffffu, bad_nf), dm = __ballot_sync(0xffffffffu, bad_dom);
   if ((threadIdx.x & 31) == 0) {
@@ -86,8 +141,9 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // one-node periodic ring) stream into a shared-memory ring by asynchronous
 // copies issued MU_DEPTH planes ahead, so several planes per block are in
 // flight while the stencil works on planes z-1, z, z+1.
-__global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, const uint8_t *__restrict__ mask,
-                                                 float *__restrict__ mu, KParams kp, int MZ) {
+__global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, const float *__restrict__ mu0,
+                                                 const uint8_t *__restrict__ mask, float *__restrict__ mu,
+                                                 KParams kp, int MZ) {
   constexpr int HX = MX + 2, HY = MY + 2, HP = HX * HY;
   constexpr int NR = MU_DEPTH + 3;  // planes z-1 .. z+1 being read, MU_DEPTH in flight, one being refilled
   __shared__ float s_r[NR][HP];
@@ -154,7 +210,7 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
       if (!(mask && mask[n])) {
         // lap = 6 sum_q w_q (rho(x + c_q) - rho(x)), split by planes
         const float lap = 6.0f * (w1(1) * (dm + (cm - c0)) + w1(0) * d0 + w1(1) * (dp + (cp - c0)));
-        mu[n] = mu0_vdw(c0, kp) - kp.kappa * lap;
+        mu[n] = mu0[n] - kp.kappa * lap;
       }
     }
     dm = d0;
@@ -578,7 +634,7 @@ void launch_mu_z(lbm_ctx *ctx) {
   const int xyb = ((kp.nx + MX - 1) / MX) * ((kp.ny + MY - 1) / MY);
   const int mz = z_chunk(xyb, kp.nz, resident_slots<k_mu_z>(MX * MY, 0), 2);
   const dim3 grid((kp.nx + MX - 1) / MX, (kp.ny + MY - 1) / MY, (kp.nz + mz - 1) / mz);
-  k_mu_z<<<grid, MX * MY, 0, ctx->stream>>>(ctx->fld.rho, ctx->mask, ctx->fld.mu, kp, mz);
+  k_mu_z<<<grid, MX * MY, 0, ctx->stream>>>(ctx->fld.rho, ctx->fld.mu0, ctx->mask, ctx->fld.mu, kp, mz);
 }
 
 void launch_moments(lbm_ctx *ctx) {
@@ -586,11 +642,15 @@ void launch_moments(lbm_ctx *ctx) {
   const Fields &d = ctx->fld;
   const int g = (kp.N + 255) / 256;
   const void *fin = ctx->f[ctx->cur];
-  if (ctx->storage == LBM_F16)
-    k_moments_v<__half><<<g, 256, 0, ctx->stream>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status,
-                                                    kp);
+  if (ctx->storage == LBM_F16 && kp.N % 2 == 0)
+    k_moments_h2<<<(kp.N / 2 + 255) / 256, 256, 0, ctx->stream>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j,
+                                                                  d.mu0, ctx->status, kp);
+  else if (ctx->storage == LBM_F16)
+    k_moments_v<__half><<<g, 256, 0, ctx->stream>>>((const __half *)fin, ctx->mask, d.sb, d.rho, d.j, d.mu0,
+                                                    ctx->status, kp);
   else
-    k_moments_v<float><<<g, 256, 0, ctx->stream>>>((const float *)fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
+    k_moments_v<float><<<g, 256, 0, ctx->stream>>>((const float *)fin, ctx->mask, d.sb, d.rho, d.j, d.mu0,
+                                                   ctx->status, kp);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,

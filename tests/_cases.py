@@ -49,6 +49,9 @@ CASES = {
     "wall_neutral_rates_noq4": dict(n=(9, 9, 10), walls=(0,), radius=3.5, sessile=True, u=(0.0, 0.01, 0.0),
                                     p=dict(q4_correction=0,
                                            omega=[1.0, 1.6, 1.2, 0.9, 1.1, 1.3, 0.8, 1.4, 1.05, 0.95, 1.5])),
+    # odd node count (FP16 moments take the one-node-per-thread path), one
+    # partial tile, uniform flow along a diagonal
+    "droplet_odd": dict(n=(9, 9, 9), walls=(), radius=3.0, u=(0.01, 0.01, 0.01), p={}),
     # rows of 16-byte multiples (tensor-copy staging of the population
     # tiles): two tiles in x and y with ragged tails, periodic (FP16 too)
     "droplet_tiles": dict(n=(40, 12, 10), walls=(), radius=4.0, u=(0.02, 0.01, -0.01), p={}),

@@ -157,7 +157,7 @@ def test_constant_shift_mode_fifty_steps(name):
     assert absd(m["u"], ref["u"]) < 1e-6
 
 
-@pytest.mark.parametrize("name", ["droplet_periodic", "droplet_tiles"])
+@pytest.mark.parametrize("name", ["droplet_periodic", "droplet_tiles", "droplet_odd"])
 def test_fp16_storage_fifty_steps(name):
     case = build(name)
     p = case["p"]
