@@ -37,11 +37,11 @@ WORKLOAD_NAME = ("moving droplet 256^3 periodic, R=32 (tanh width 2), U=(0.05,0.
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
 # storage, valid only while the kernel sources hash to `src`.  The capture is
-# `--profile-case step128` (k_fused<float>, 128^3, 2,097,152 nodes): 289.40 MB
-# read + 194.64 MB written = 230.8 B per node, scaled by 8 to one 256^3 launch
+# `--profile-case step128` (k_fused<float>, 128^3, 2,097,152 nodes): 289.27 MB
+# read + 195.09 MB written = 231.0 B per node, scaled by 8 to one 256^3 launch
 # (the kernel's traffic is proportional to the nodes it updates).
-NCU_TRAFFIC = {"f32": {"bytes_per_launch": 3872299008, "bytes_per_lu": 230.8,
-                       "captured_on": "128^3, scaled x8", "src": "6c0e0710673f9bad"}}
+NCU_TRAFFIC = {"f32": {"bytes_per_launch": 3874916352, "bytes_per_lu": 231.0,
+                       "captured_on": "128^3, scaled x8", "src": "319db43f2eccc2df"}}
 
 
 def src_hash() -> str:
@@ -242,6 +242,54 @@ ADJ_WORKLOAD = ("differentiable droplet on a wall 64^3 (solid planes z=0, z=63),
                 "kappa=0.01 diverges), phi-wetting 1.2, rates 1, contact-line radius objective")
 
 
+def run_configs(local, steps: int = 200):
+    """MLUPS of the other workload configurations (device-timed, CUDA events,
+    after 20 warm-up steps): the flat interface 8x8x128, a stationary 64^3
+    droplet (R = 8, 0.85 T_c) and the 256x256x128 wall with a hemisphere
+    (R = 40, interface width 2 as for the moving droplet, phi-wetting 1.2,
+    0.85 T_c), each with FP32 and FP16 storage."""
+    import numpy as np
+    import torch
+
+    from paper_2504_03819_gb300 import Domain, Params
+    from paper_2504_03819_gb300 import binding as Bd
+    from paper_2504_03819_gb300 import inputs as I
+    out = {}
+    base = dict(a=9.0 / 49.0, b=2.0 / 21.0, R=1.0, t=0.85, kappa=0.01)
+    cases = {
+        "flat 8x8x128": ((8, 8, 128), {}, None),
+        "droplet 64^3 R=8": ((64, 64, 64), {}, None),
+        "wall 256x256x128 R=40 phi=1.2": ((256, 256, 128), dict(wetting_mode=Bd.WET_PHI, wetting_value=1.2), (0, 127)),
+    }
+    for name, (n, kw, walls) in cases.items():
+        nx, ny, nz = n
+        p = Params.vdw(base["a"], base["b"], base["R"], base["t"], base["kappa"], **kw)
+        mask = I.wall_mask(nx, ny, nz, planes=walls) if walls else None
+        if name.startswith("flat"):
+            rho0 = np.repeat(np.repeat(I.slab(1, 1, nz, 64, p.rho_l, p.rho_v), nx, 2), ny, 1)
+        elif walls:
+            rho0 = I.sessile_droplet(nx, ny, nz, 40.0, p.rho_l, p.rho_v, wall_z=0.5, width=2.0)
+        else:
+            rho0 = I.droplet(nx, ny, nz, 8.0, p.rho_l, p.rho_v)
+        res = {}
+        for storage in ("f32", "f16"):
+            d = Domain(nx, ny, nz, storage, solid_mask=mask, device=f"cuda:{local}")
+            d.set_params(p)
+            d.set_state(torch.from_numpy(rho0.astype(np.float32)))
+            d.step(20)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(d.stream)
+            d.step(steps)
+            e1.record(d.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[storage] = {"MLUPS": nx * ny * nz / (ms * 1e-3) / 1e6, "ms_per_step": ms, "status": d.sync_status()}
+            d.close()
+        out[name] = res
+    return out
+
+
 def run_adjoint(args, local):
     """Forward time of `adjoint_steps` steps against the time of the full
     adjoint sweep (segment recompute from checkpoints every 100 steps,
@@ -361,6 +409,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the MLUPS of the other workload configurations")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.profile_case:
@@ -391,6 +440,7 @@ def main():
     __graft_entry__.build()
     res, e2e, peak, peak_src, N = run_ours(args, world, rank, local)
     adj = run_adjoint(args, local) if args.adjoint_steps > 0 else None
+    configs = run_configs(local) if not args.no_configs else None
     if rank != 0:
         return
     r32, r16 = res["f32"], res["f16"]
@@ -421,6 +471,7 @@ def main():
                        "collide_achieved_GBps": r16["achieved"], "status": r16["status"]},
         "kernel_ms_per_step": {k: v[0] / max(v[1], 1) * (v[1] / args.steps) for k, v in r32["prof"].items() if v[1]},
         "adjoint": adj,
+        "other_configs": configs,
         "e2e": e2e, "gpu_launches": r32["launches"], "clocks": r32["clocks"], "cpu_baseline": cpu,
         "status": r32["status"],
     }
