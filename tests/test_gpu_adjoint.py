@@ -190,3 +190,27 @@ def test_adjoint_step_bitwise_deterministic():
         d.close()
     assert torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("name", ["droplet_tiles", "wall_tiles"])
+def test_one_adjoint_step_fp16_storage(name):
+    """The adjoint with FP16 population storage: the oracle's reverse mode at
+    the populations the FP16 state holds (read back through
+    lbm_get_populations), so both sides linearise the same state."""
+    case = build(name)
+    fr = perturbed(case, oracle_init(case), seed=61)
+    nx, ny, nz = case["n"]
+    d = Domain(nx, ny, nz, "f16", solid_mask=case["mask"] if case["mask"].any() else None)
+    d.set_params(case["p"])
+    d.set_populations(fr.float())
+    held = d.get_populations().double().cpu()
+    g = torch.Generator().manual_seed(12)
+    fluid = torch.from_numpy(~case["mask"].astype(bool)).to(DT)
+    lam = (torch.randn(27, nz, ny, nx, generator=g, dtype=DT) * fluid).float().double()
+    raw = d.get_state().clone()
+    grad = torch.zeros(Bd.NGRAD, dtype=DT, device="cuda")
+    lt = d.adjoint_step(raw, lam.float().cuda(), grad)
+    ref_lt, ref_g = oracle_theta_grads(case, held, lam)
+    assert relmax(lt, ref_lt) < 1e-4
+    scale = float(ref_g.abs().max())
+    assert float((grad.cpu() - ref_g).abs().max()) / scale < 1e-4
