@@ -657,7 +657,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+// cuTensorMapEncodeTiled of the CUDA driver API, resolved once through the runtime
 EncodeTiledFn encode_tiled() {
   static std::once_flag once;
   static EncodeTiledFn fn = nullptr;
