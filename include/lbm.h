@@ -168,7 +168,11 @@ int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0);
  * (Eq. 36), force (Eq. 12), corrections (Eqs. 27-28), central-moment
  * collision (Eqs. 19-26) and streaming (Eq. 10) with halfway bounce-back.
  * Enqueues only; a density that is non-finite or outside (0, 1/b) at the
- * start of any step sets a status flag read by lbm_sync_status.
+ * start of any step sets a status flag read by lbm_sync_status.  Groups of
+ * 16 steps run as one CUDA graph, captured on the context's own stream at
+ * the first such call from each buffer (and again after lbm_set_params or
+ * lbm_set_wall_velocity) and launched into the context's stream; results
+ * are bitwise those of single steps.  Not while per-kernel profiling is on.
  */
 int lbm_step(lbm_ctx *ctx, int n);
 
@@ -282,7 +286,12 @@ size_t lbm_adjoint_pool_bytes(const lbm_ctx *ctx);
  * dJ/df(t0); lam_tmp: device, 27*N floats of scratch; grad_params:
  * accumulated as in lbm_adjoint_step.  The context's current state becomes
  * ckpt.  Equivalent to n calls of lbm_adjoint_step on the recomputed states
- * (up to FP32 rounding of the fields).
+ * (up to FP32 rounding of the fields).  The sweep between the checkpoint
+ * copy-in and the restore runs as one CUDA graph, captured at the first call
+ * with a given n, state_pool, lam, lam_tmp and grad_params (the two most
+ * recent are kept; lbm_set_params and lbm_set_wall_velocity discard them);
+ * results are bitwise those of the direct launches, which run instead while
+ * per-kernel profiling is on.
  */
 int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool, float *lam, float *lam_tmp,
                         double *grad_params);

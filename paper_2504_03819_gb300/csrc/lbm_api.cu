@@ -207,6 +207,7 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
   if (!ctx) return LBM_ERR_ARG;
   int rc = validate(ctx, p);
   if (rc != LBM_OK) return rc;
+  drop_step_graphs(ctx);  // the kernels take the parameters by value
   ctx->params = *p;
   KParams &k = ctx->kp;
   k.RT = (float)(p->R * p->T);
@@ -260,6 +261,7 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
 int lbm_set_wall_velocity(lbm_ctx *ctx, const float *wall_u) {
   if (!ctx) return LBM_ERR_ARG;
   if (wall_u && !ctx->mask) return fail(ctx, LBM_ERR_STATE, "wall velocities need a domain with a solid mask");
+  if (wall_u != ctx->wall_u) drop_step_graphs(ctx);
   ctx->wall_u = wall_u;
   return LBM_OK;
 }
@@ -276,11 +278,78 @@ int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0) {
   return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Graph of GRAPH_STEPS steps from the current buffer, captured once on the
+// context's private stream (the kernels and their arguments are recorded,
+// not run); null when capture is not possible, so the caller launches
+// directly.
+cudaGraphExec_t step_graph(lbm_ctx *ctx) {
+  const int parity = ctx->cur;
+  if (ctx->step_graph[parity]) return ctx->step_graph[parity];
+  if (!ctx->capture_stream && cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->capture_stream = nullptr;
+    return nullptr;
+  }
+  cudaStream_t user = ctx->stream;
+  const long long l0 = ctx->launches;
+  if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctx->stream = ctx->capture_stream;
+  for (int i = 0; i < GRAPH_STEPS; ++i) launch_step(ctx);
+  ctx->stream = user;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = cudaStreamEndCapture(ctx->capture_stream, &g) == cudaSuccess && g &&
+                  cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  ctx->graph_launches = ctx->launches - l0;
+  ctx->launches = l0;  // counted when the graph runs
+  if (!ok) return nullptr;
+  ctx->step_graph[parity] = exec;
+  return exec;
+}
+
+}  // namespace
+
+namespace lbm {
+void drop_step_graphs(lbm_ctx *ctx) {
+  for (cudaGraphExec_t &e : ctx->step_graph) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+  for (SegmentGraph &g : ctx->seg_graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = SegmentGraph{};
+  }
+}
+}  // namespace lbm
+
+extern "C" {
+
 int lbm_step(lbm_ctx *ctx, int n) {
   if (!ctx) return LBM_ERR_ARG;
   if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
   if (!ctx->have_state) return fail(ctx, LBM_ERR_STATE, "no state: call lbm_set_state first");
   cudaGetLastError();
+  // whole groups of GRAPH_STEPS steps replay a captured graph (one launch
+  // instead of three to five per step); per-kernel profiling needs the
+  // individual launches
+  while (n >= GRAPH_STEPS && !ctx->prof_on) {
+    cudaGraphExec_t g = step_graph(ctx);
+    if (!g || cudaGraphLaunch(g, ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    ctx->launches += ctx->graph_launches;
+    n -= GRAPH_STEPS;
+  }
   for (int i = 0; i < n; ++i) launch_step(ctx);
   return check_cuda(ctx, "lbm_step");
 }
@@ -392,32 +461,44 @@ size_t lbm_adjoint_pool_bytes(const lbm_ctx *ctx) {
   return align_up(align_up(lbm_state_bytes(ctx)) + 11 * (size_t)ctx->N * sizeof(float));
 }
 
-int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool, float *lam, float *lam_tmp,
-                        double *grad_params) {
-  if (!ctx || !ckpt || n < 1 || !state_pool || !lam || !lam_tmp || !grad_params || lam == lam_tmp)
-    return LBM_ERR_ARG;
-  if (!ctx->have_params) return fail(ctx, LBM_ERR_STATE, "lbm_set_params must come first");
-  const size_t pops = 27 * (size_t)ctx->N * (ctx->storage == LBM_F16 ? 2 : 4);
-  const bool rest = ctx->kp.shift_mode == LBM_SHIFT_REST;
-  const size_t sbb = rest ? 2 * (size_t)ctx->N * sizeof(float) : 0, sbytes = pops + sbb;
-  const size_t stride = lbm_adjoint_pool_bytes(ctx), cap_off = align_up(sbytes);
-  char *pool = (char *)state_pool;
-  auto slot = [&](int i) { return pool + (size_t)i * stride; };
+}  // extern "C"
+
+namespace {
+
+struct SegmentLayout {
+  size_t pops, sbb, sbytes, stride, cap_off;
+  bool rest;
+};
+
+SegmentLayout segment_layout(const lbm_ctx *ctx) {
+  SegmentLayout L;
+  L.pops = 27 * (size_t)ctx->N * (ctx->storage == LBM_F16 ? 2 : 4);
+  L.rest = ctx->kp.shift_mode == LBM_SHIFT_REST;
+  L.sbb = L.rest ? 2 * (size_t)ctx->N * sizeof(float) : 0;
+  L.sbytes = L.pops + L.sbb;
+  L.stride = lbm_adjoint_pool_bytes(ctx);
+  L.cap_off = align_up(L.sbytes);
+  return L;
+}
+
+// The sweep of one segment after its checkpoint is in pool slot 0 (and its
+// shift bases in fld.sb): recompute of the states and their fields, the
+// adjoint steps from the last state down to the first, the gradient
+// reduction.  Enqueued on ctx->stream; leaves ctx->f / ctx->cur pointing
+// into the pool (the caller restores them).
+void enqueue_segment(lbm_ctx *ctx, int n, char *pool, float *lam, float *lam_tmp, double *grad) {
+  const SegmentLayout L = segment_layout(ctx);
+  auto slot = [&](int i) { return pool + (size_t)i * L.stride; };
   cudaStream_t s = ctx->stream;
-  cudaGetLastError();
-  cudaMemcpyAsync(pool, ckpt, sbytes, cudaMemcpyDeviceToDevice, s);
-  if (rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + pops, sbb, cudaMemcpyDeviceToDevice, s);
-  void *own0 = ctx->f[0], *own1 = ctx->f[1];
-  const int own_cur = ctx->cur;
   // recompute: step i reads slot i-1, writes slot i and captures the fields
   // of state i-1 into slot i-1
   for (int i = 1; i < n; ++i) {
     ctx->f[ctx->cur] = slot(i - 1);
     ctx->f[1 - ctx->cur] = slot(i);
-    ctx->capture = (float *)(slot(i - 1) + cap_off);
+    ctx->capture = (float *)(slot(i - 1) + L.cap_off);
     launch_step(ctx);
     ctx->capture = nullptr;
-    if (rest) cudaMemcpyAsync(slot(i) + pops, ctx->fld.sb, sbb, cudaMemcpyDeviceToDevice, s);
+    if (L.rest) cudaMemcpyAsync(slot(i) + L.pops, ctx->fld.sb, L.sbb, cudaMemcpyDeviceToDevice, s);
   }
   // adjoint steps from t0+n-1 down to t0, lambda ping-pong; the last state
   // of the segment was not stepped, so its fields are recomputed
@@ -427,24 +508,94 @@ int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool,
     ctx->f[ctx->cur] = slot(k);
     cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
     if (k == n - 1) {
-      if (rest) cudaMemcpyAsync(ctx->fld.sb, slot(k) + pops, sbb, cudaMemcpyDeviceToDevice, s);
+      if (L.rest) cudaMemcpyAsync(ctx->fld.sb, slot(k) + L.pops, L.sbb, cudaMemcpyDeviceToDevice, s);
       launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout);
     } else {
-      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, (const float *)(slot(k) + cap_off),
-                          rest ? (const float *)(slot(k) + pops) : ctx->fld.sb);
+      launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, (const float *)(slot(k) + L.cap_off),
+                          L.rest ? (const float *)(slot(k) + L.pops) : ctx->fld.sb);
     }
     float *t = lin;
     lin = lout;
     lout = t;
   }
-  launch_adjoint_partials_reduce(ctx, grad_params);
+  launch_adjoint_partials_reduce(ctx, grad);
   if (lin != lam) cudaMemcpyAsync(lam, lin, 27 * (size_t)ctx->N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+}
+
+// The segment sweep as a CUDA graph, captured once per (length, buffers) on
+// the context's private stream; null when capture is not possible.
+cudaGraphExec_t segment_graph(lbm_ctx *ctx, int n, char *pool, float *lam, float *lam_tmp, double *grad) {
+  for (const SegmentGraph &g : ctx->seg_graphs)
+    if (g.exec && g.n == n && g.pool == pool && g.lam == lam && g.lam_tmp == lam_tmp && g.grad == grad) {
+      ctx->launches += g.launches;
+      return g.exec;
+    }
+  if (!ctx->capture_stream && cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->capture_stream = nullptr;
+    return nullptr;
+  }
+  void *own0 = ctx->f[0], *own1 = ctx->f[1];
+  const int own_cur = ctx->cur;
+  cudaStream_t user = ctx->stream;
+  const long long l0 = ctx->launches;
+  if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctx->stream = ctx->capture_stream;
+  enqueue_segment(ctx, n, pool, lam, lam_tmp, grad);
+  ctx->stream = user;
+  ctx->f[0] = own0;
+  ctx->f[1] = own1;
+  ctx->cur = own_cur;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = cudaStreamEndCapture(ctx->capture_stream, &graph) == cudaSuccess && graph &&
+                  cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  const long long counted = ctx->launches - l0;
+  if (!ok) {
+    ctx->launches = l0;
+    return nullptr;
+  }
+  SegmentGraph &g = ctx->seg_graphs[ctx->seg_next];
+  ctx->seg_next = (ctx->seg_next + 1) % SEG_GRAPHS;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g = SegmentGraph{n, pool, lam, lam_tmp, grad, exec, counted};
+  return exec;  // the capture's launch count stands for this first replay
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool, float *lam, float *lam_tmp,
+                        double *grad_params) {
+  if (!ctx || !ckpt || n < 1 || !state_pool || !lam || !lam_tmp || !grad_params || lam == lam_tmp)
+    return LBM_ERR_ARG;
+  if (!ctx->have_params) return fail(ctx, LBM_ERR_STATE, "lbm_set_params must come first");
+  const SegmentLayout L = segment_layout(ctx);
+  char *pool = (char *)state_pool;
+  cudaStream_t s = ctx->stream;
+  cudaGetLastError();
+  cudaMemcpyAsync(pool, ckpt, L.sbytes, cudaMemcpyDeviceToDevice, s);
+  if (L.rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + L.pops, L.sbb, cudaMemcpyDeviceToDevice, s);
+  void *own0 = ctx->f[0], *own1 = ctx->f[1];
+  const int own_cur = ctx->cur;
+  // one graph launch per segment (per-kernel profiling needs the launches)
+  cudaGraphExec_t g = ctx->prof_on ? nullptr : segment_graph(ctx, n, pool, lam, lam_tmp, grad_params);
+  if (!g || cudaGraphLaunch(g, s) != cudaSuccess) {
+    cudaGetLastError();
+    enqueue_segment(ctx, n, pool, lam, lam_tmp, grad_params);
+  }
   // the context's own buffers hold ckpt afterwards
   ctx->f[0] = own0;
   ctx->f[1] = own1;
   ctx->cur = own_cur;
-  cudaMemcpyAsync(ctx->f[ctx->cur], ckpt, pops, cudaMemcpyDeviceToDevice, s);
-  if (rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + pops, sbb, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(ctx->f[ctx->cur], ckpt, L.pops, cudaMemcpyDeviceToDevice, s);
+  if (L.rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + L.pops, L.sbb, cudaMemcpyDeviceToDevice, s);
   ctx->have_state = 1;
   return check_cuda(ctx, "lbm_adjoint_segment");
 }
@@ -470,6 +621,8 @@ void lbm_destroy(lbm_ctx *ctx) {
     harvest_profile(ctx);
   }
   for (cudaEvent_t e : ctx->prof_free) cudaEventDestroy(e);
+  drop_step_graphs(ctx);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   cudaGetLastError();
   delete ctx;
 }

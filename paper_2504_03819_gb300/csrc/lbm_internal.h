@@ -76,6 +76,17 @@ struct TmapEntry {
 };
 constexpr int TMAP_CACHE = 4;
 
+// A captured adjoint segment sweep and the buffers it was captured with.
+struct SegmentGraph {
+  int n;
+  void *pool;
+  float *lam, *lam_tmp;
+  double *grad;
+  cudaGraphExec_t exec;
+  long long launches;
+};
+constexpr int SEG_GRAPHS = 2;
+
 struct ProfEvent {
   int id;
   cudaEvent_t start, stop;
@@ -112,12 +123,21 @@ struct lbm_ctx {
   long long prof_n[lbm::K_COUNT];
   lbm::TmapEntry tmaps[lbm::TMAP_CACHE];
   int tmap_next;
+  // CUDA graphs of lbm::GRAPH_STEPS steps, one per starting buffer, captured
+  // on a private stream and launched into `stream`; rebuilt after any change
+  // of the parameters or wall velocities the kernels take by value
+  cudaStream_t capture_stream;
+  cudaGraphExec_t step_graph[2];
+  long long graph_launches;  // kernel launches one graph replays
+  lbm::SegmentGraph seg_graphs[lbm::SEG_GRAPHS];
+  int seg_next;
   std::string err;
 };
 
 namespace lbm {
 
 constexpr int RED_BLOCKS = 1024;
+constexpr int GRAPH_STEPS = 16;  // steps per captured graph (even: the buffers return to their start)
 
 // Node-parallel adjoint kernels run on 3-D grids of 32 x ADJ_BY x 1 blocks
 // (x fastest); the number of blocks sizes their per-block partial sums.
@@ -155,6 +175,7 @@ void launch_adjoint_partials_reduce(lbm_ctx *ctx, double *grad);
 void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, double *grad, float *grad_rho0);
 void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad);
 void launch_set_populations(lbm_ctx *ctx, const float *in);
+void drop_step_graphs(lbm_ctx *ctx);  // after a change the captured step graphs would miss (lbm_api.cu)
 const char *kernel_name(int id);
 
 // Counts a kernel launch of the context and, when per-kernel profiling is on,
