@@ -222,6 +222,8 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
   k.g3 = 2.0f * k.om_h[3] * (1.0f / 3.0f);
   k.g5 = k.om_h[9] * (1.0f / 3.0f) * (1.0f / 3.0f);
   k.o10e = k.om[10] * (1.0f / 3.0f) * (1.0f / 3.0f);
+  const float hs[8] = {k.om_c[0], k.om_h[0], k.om_c[5], k.om_c[8], k.om_c[9], k.g5, k.om_c[10], k.o10e};
+  for (int i = 0; i < 8; ++i) k.hs[i] = hs[i] * (i < 2 ? 0.5f : 0.125f);
   k.nu = (float)p->nu;
   k.q4 = p->q4_correction;
   k.rho_shift = (float)p->rho_shift;

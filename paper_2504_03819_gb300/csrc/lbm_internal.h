@@ -20,6 +20,10 @@ struct KParams {
   float om[11];
   float om_c[11], om_h[11];  // 1 - omega_i and 1 - omega_i / 2 (collision factors)
   float g3, g5, o10e;        // 2 (1 - omega_3/2) / 3, (1 - omega_9/2) / 9, omega_10 / 9
+  // the factors above that multiply a post-collision moment directly, scaled
+  // for the halved moments of from_central_h (exact powers of two):
+  // om_c[0]/2, om_h[0]/2, om_c[5]/8, om_c[8]/8, om_c[9]/8, g5/8, om_c[10]/8, o10e/8
+  float hs[8];
   float nu;        // > 0: omega_1 per node from 1/omega_1 = rho nu / p_m + 1/2
   int q4;          // fourth-order correction on/off
   float rho_shift; // rho_0 of the stored populations f_i - w_i rho_0

@@ -274,8 +274,10 @@ template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return _
 // tensor copy issued a plane ahead (tmap describes fin as [27][nz][ny][nx]);
 // otherwise each thread loads its node's populations directly.  WALLV: the
 // walls move (wall_u holds the solid nodes' velocities); compiled out of the
-// resting-wall instantiations, whose registers it would raise.
-template <typename T, bool MASK, bool TMA, bool WALLV>
+// resting-wall instantiations, whose registers it would raise.  UNIT: every
+// rate but omega_1 is 1, so the collision reads only seven central moments
+// (to_central_unit, collide_cm_unit).
+template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT>
 __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
@@ -541,9 +543,15 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
 
 #pragma unroll
     for (int q = 0; q < 27; ++q) f[q] += rest ? shift_rest(q, rb, cb) : weight_of(q) * kp.rho_shift;
-    to_central(f, ux, uy, uz);
-    collide_cm(f, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
-    from_central(f, ux, uy, uz);
+    // post-collision moments halved as from_central_h takes them
+    if (UNIT) {
+      to_central_unit(f, ux, uy, uz);
+      collide_cm_unit<true>(f, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
+    } else {
+      to_central(f, ux, uy, uz);
+      collide_cm<true>(f, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp);
+    }
+    from_central_h(f, ux, uy, uz);
 
     // push with bounce-back; shifts keyed by the destination's fields
     const int oz[3] = {z == 0 ? (nz - 1) * nxy : -nxy, 0, z == nz - 1 ? -(nz - 1) * nxy : nxy};
@@ -698,18 +706,33 @@ const CUtensorMap *population_tmap(lbm_ctx *ctx, const void *p) {
   return e.ok ? &e.map : nullptr;
 }
 
-template <typename T, bool MASK, bool TMA, bool WALLV>
-void launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
+template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT>
+void launch_fused_u(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
   const KParams &kp = ctx->kp;
   const Fields &d = ctx->fld;
   constexpr size_t sm = fused_smem_size<T>(TMA);
-  ensure_smem<k_fused<T, MASK, TMA, WALLV>>(sm);
+  constexpr auto K = k_fused<T, MASK, TMA, WALLV, UNIT>;
+  ensure_smem<K>(sm);
   const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
-  const int tz = z_chunk(xyb, kp.nz, resident_slots<k_fused<T, MASK, TMA, WALLV>>(NT, sm), 2);
+  const int tz = z_chunk(xyb, kp.nz, resident_slots<K>(NT, sm), 2);
   const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
-  k_fused<T, MASK, TMA, WALLV><<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j,
-                                                              d.mu, d.sb, ctx->status, ctx->capture,
-                                                              WALLV ? ctx->wall_u : nullptr, kp, tz, map);
+  K<<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j, d.mu, d.sb, ctx->status,
+                                   ctx->capture, WALLV ? ctx->wall_u : nullptr, kp, tz, map);
+}
+
+// every rate but omega_1 equal to 1 (exactly: each 1 - omega_i is 0)
+bool unit_rates(const KParams &kp) {
+  for (int i = 0; i < 11; ++i)
+    if (i != 1 && kp.om_c[i] != 0.0f) return false;
+  return true;
+}
+
+template <typename T, bool MASK, bool TMA, bool WALLV>
+void launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
+  if (unit_rates(ctx->kp))
+    launch_fused_u<T, MASK, TMA, WALLV, true>(ctx, fin, fout, map);
+  else
+    launch_fused_u<T, MASK, TMA, WALLV, false>(ctx, fin, fout, map);
 }
 
 template <typename T>
