@@ -321,7 +321,9 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     const int k = tid + s * NT;
     xy1[s] = k < H1P ? pmod(x0 + k % H1X - 1, nx) + nx * pmod(y0 + k / H1X - 1, ny) : 0;
   }
-  auto zoff = [&](int z) { return (size_t)nxy * pmod(z, nz); };
+  // z runs over [z0 - 2, z1 + 1]: one period of wrap once nz >= 3 (no
+  // division in the loop); thinner domains take the general modulus
+  auto zoff = [&](int z) { return (size_t)nxy * (nz >= 3 ? wrap(z, nz) : pmod(z, nz)); };
 
   // planes are fetched into registers one iteration before they are stored
   // to shared memory, so their DRAM latency overlaps a whole plane of work
@@ -342,8 +344,8 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       if (MASK) psolid[s] = (ok && mask) ? mask[g] : (uint8_t)0;
     }
   };
-  auto store = [&](int zm, int zr) {
-    float *dm = S.mu[r5(zm)];
+  auto store = [&](int s5, int zr) {  // s5: ring slot of the mu' plane
+    float *dm = S.mu[s5];
 #pragma unroll
     for (int s = 0; s < S2; ++s)
       if (tid + s * NT < H2P) dm[tid + s * NT] = pmu[s];
@@ -362,15 +364,28 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   };
   // F, u, phi at every one-node-ring position of plane z (u, F kept for the
   // tile positions)
-  auto fields = [&](int z, bool keep_uF) {
-    const int rg = r4(z), rp = r3(z);
-    const float *m0 = S.mu[r5(z - 1)], *m1 = S.mu[r5(z)], *m2 = S.mu[r5(z + 1)];
-    for (int k = tid; k < H1P; k += NT) {
-      const int hx = k % H1X, hy = k / H1X;
+  // this thread's one-node-ring positions k = tid, tid + NT: position in the
+  // two-node ring and tile index (-1 off the tile), fixed for the column
+  static_assert(S1 == 2, "two ring slots per thread");
+  int fc[2], ft[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int k = tid + s * NT, hx = k % H1X, hy = k / H1X;
+    fc[s] = (hy + 1) * H2X + hx + 1;
+    ft[s] = (hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) ? (hy - 1) * TX + hx - 1 : -1;
+  }
+  // (a5m, a5, a5p: ring slots of mu' planes z-1 .. z+1; rp: slot of plane z
+  // in the three-plane rings)
+  auto fields = [&](int z, bool keep_uF, int a5m, int a5, int a5p, int rp) {
+    const int rg = r4(z);
+    const float *m0 = S.mu[a5m], *m1 = S.mu[a5], *m2 = S.mu[a5p];
+#pragma unroll 1
+    for (int k = tid, s = 0; k < H1P; k += NT, ++s) {
+      const int fcs = s ? fc[1] : fc[0], fts = s ? ft[1] : ft[0];
       float phx = 0.0f, phy = 0.0f, phz = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f, Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
       float sh0 = 0.0f, sh1 = 0.0f, sh2 = 0.0f, sh3 = 0.0f;
       if (!MASK || !S.solid[rg][k]) {
-        const int c = (hy + 1) * H2X + hx + 1;  // position in the two-node ring
+        const int c = fcs;  // position in the two-node ring
         const float mc = m1[c];
         // sum_q w_q c_q mu'(x + c_q), one partial sum per plane and axis so
         // the dependent chains stay short (sum_q w_q c_q = 0: the centre
@@ -415,8 +430,8 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
         S.shift[rp][2][k] = sh2;
         S.shift[rp][3][k] = sh3;
       }
-      if (keep_uF && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
-        const int t = (hy - 1) * TX + hx - 1;
+      if (keep_uF && fts >= 0) {
+        const int t = fts;
         float *o = S.uF[r2(z)][0];
         o[t] = ux;
         o[NT + t] = uy;
@@ -438,22 +453,35 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   // memory, mu'(z0+2) and rho/j(z0+1) in registers; phi of z0-1 and z0,
   // u/F of z0
   fetch(z0 - 2, z0 - 1);
-  store(z0 - 2, z0 - 1);
+  store(r5(z0 - 2), z0 - 1);
   fetch(z0 - 1, z0);
-  store(z0 - 1, z0);
+  store(r5(z0 - 1), z0);
   fetch(z0, z0);
-  store(z0, z0);
+  store(r5(z0), z0);
   fetch(z0 + 1, z0);
-  store(z0 + 1, z0);
+  store(r5(z0 + 1), z0);
   fetch(z0 + 2, z0 + 1);
   __syncthreads();
-  fields(z0 - 1, false);
-  fields(z0, true);
+  fields(z0 - 1, false, r5(z0 - 2), r5(z0 - 1), r5(z0), r3(z0 - 1));
+  fields(z0, true, r5(z0 - 1), r5(z0), r5(z0 + 1), r3(z0));
 
   const int c1 = (ty + 1) * H1X + tx + 1;
-  for (int z = z0; z < z1; ++z) {
+  // ring slots of planes z, z+1, z+2 (mu') and z-1, z, z+1 (phi, shift),
+  // carried from plane to plane instead of recomputed (no division)
+  int i5a = r5(z0), i5b = r5(z0 + 1), i5c = r5(z0 + 2);
+  int i3m = r3(z0 - 1), i3a = r3(z0), i3b = r3(z0 + 1);
+  auto advance = [&]() {
+    i5a = i5b;
+    i5b = i5c;
+    i5c = i5c == 4 ? 0 : i5c + 1;
+    const int t = i3m;
+    i3m = i3a;
+    i3a = i3b;
+    i3b = t;
+  };
+  for (int z = z0; z < z1; ++z, advance()) {
     // publish mu'(z+2), rho/j(z+1); prefetch mu'(z+3), rho/j(z+2)
-    store(z + 2, z + 1);
+    store(i5c, z + 1);
     if (z + 1 < z1) fetch(z + 3, z + 2);
     // populations of this node
     const int n = x + nx * y + nxy * z;
@@ -489,12 +517,12 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       }
       __syncthreads();
     }
-    fields(z + 1, true);
+    fields(z + 1, true, i5a, i5b, i5c, i3b);
     __syncthreads();
     if (!active) {
       if (cap && inside) {  // solid node: its wetting rho and mu', no flow
         cap[n] = S.rho[r4(z)][c1];
-        cap[N + n] = S.mu[r5(z)][(ty + 2) * H2X + tx + 2];
+        cap[N + n] = S.mu[i5a][(ty + 2) * H2X + tx + 2];
 #pragma unroll
         for (int c = 0; c < 9; ++c) cap[(2 + c) * N + n] = 0.0f;
       }
@@ -503,7 +531,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
 
     // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa phi_a(x + c_q), partial sums
     // per plane
-    const float *p0 = S.phi[r3(z - 1)][0], *p1 = S.phi[r3(z)][0], *p2 = S.phi[r3(z + 1)][0];
+    const float *p0 = S.phi[i3m][0], *p1 = S.phi[i3a][0], *p2 = S.phi[i3b][0];
     float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f}, qz[2] = {0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
@@ -523,7 +551,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     const float ux = uF[t], uy = uF[NT + t], uz = uF[2 * NT + t];
     const float Fx = uF[3 * NT + t], Fy = uF[4 * NT + t], Fz = uF[5 * NT + t];
     const float r_own = S.rho[r4(z)][c1];
-    const float mu_own = S.mu[r5(z)][(ty + 2) * H2X + tx + 2];
+    const float mu_own = S.mu[i5a][(ty + 2) * H2X + tx + 2];
     if (cap) {  // fields of this state for the adjoint: rho, mu', u, F, Q
       cap[n] = r_own;
       cap[N + n] = mu_own;
@@ -541,8 +569,12 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     float om1 = kp.om[1];
     if (kp.nu > 0.0f) om1 = 1.0f / (r_own * kp.nu / pm + 0.5f);
 
+    // the storage shift (basis rb, cb; rho_0 and 0 for the constant shift)
+    // added back: f* - s rounded on the store and + s here restore f* exactly
+    // wherever f* is within a factor two of s, which is why the shift is
+    // added per population and not to the moments
 #pragma unroll
-    for (int q = 0; q < 27; ++q) f[q] += rest ? shift_rest(q, rb, cb) : weight_of(q) * kp.rho_shift;
+    for (int q = 0; q < 27; ++q) f[q] += shift_rest(q, rb, cb);
     // post-collision moments halved as from_central_h takes them
     if (UNIT) {
       to_central_unit(f, ux, uy, uz);
@@ -574,7 +606,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
         }
         store_pop<T>(fout + (size_t)(26 - q) * N + n, f[q] - sh);
       } else {
-        if (rest) sh = S.shift[r3(z + cz)][cx * cx + cy * cy + cz * cz][hk];
+        if (rest) sh = S.shift[cz < 0 ? i3m : (cz == 0 ? i3a : i3b)][cx * cx + cy * cy + cz * cz][hk];
         const int m = n + ox[cx + 1] + oy[cy + 1] + oz[cz + 1];
         store_pop<T>(fout + q * N + m, f[q] - sh);
       }
