@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
   constexpr int HX = MX + 2, HY = MY + 2, HP = HX * HY;
   constexpr int NR = MU_DEPTH + 3;  // planes z-1 .. z+1 being read, MU_DEPTH in flight, one being refilled
   __shared__ float s_r[NR][HP];
+  __shared__ float s_m0[NR][MX * MY];  // mu0 of the tile, copied with its plane
   const int tx = threadIdx.x % MX, ty = threadIdx.x / MX;
   const int x0 = blockIdx.x * MX, y0 = blockIdx.y * MY, z0 = blockIdx.z * MZ;
   const int z1 = min(z0 + MZ, kp.nz);
@@ -161,22 +162,26 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
     slot_xy[s] = k < HP ? pmod(x0 + hx - 1, kp.nx) + kp.nx * pmod(y0 + hy - 1, kp.ny) : 0;
   }
   auto ring = [&](int z) { return (z - z0 + 1 + NR) % NR; };  // z >= z0 - 1
-  // asynchronous copy of plane z into its ring slot (one commit group per
-  // plane, empty past the end of the column)
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < kp.nx && y < kp.ny;
+  const int nxy0 = x + kp.nx * y;
+  // asynchronous copy of plane z into its ring slot, with mu0 of the tile
+  // nodes of the planes the block updates (one commit group per plane,
+  // empty past the end of the column)
   auto issue = [&](int z, int slot) {
     if (z <= z1) {
-      const float *src = rho + (size_t)nxy * pmod(z, kp.nz);
+      // z in [z0 - 1, z1]: one period of wrap (no division) once nz >= 2
+      const float *src = rho + (size_t)nxy * (kp.nz >= 2 ? wrap(z, kp.nz) : pmod(z, kp.nz));
       float *dst = s_r[slot];
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
         const int k = threadIdx.x + s * MX * MY;
         if (k < HP) cp_async4(dst + k, src + slot_xy[s]);
       }
+      if (inside && z >= z0 && z < z1) cp_async4(&s_m0[slot][threadIdx.x], mu0 + (size_t)nxy * z + nxy0);
     }
     cp_async_commit();
   };
-  const int x = x0 + tx, y = y0 + ty;
-  const bool inside = x < kp.nx && y < kp.ny;
   // D(z') = sum_{cx,cy} w1 w1 (rho(x+cx, y+cy, z') - rho(x, y, z')) about
   // each plane's own centre: small numbers, accurate in FP32
   auto plane_sum = [&](int slot, float &centre) {
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
   float dm, cm, d0, c0, dp, cp;
   dm = plane_sum(ring(z0 - 1), cm);
   d0 = plane_sum(ring(z0), c0);
-  int slot_in = ring(z0 + MU_DEPTH + 1), slot_next = ring(z0 + 1);  // rotate with z
+  int slot_in = ring(z0 + MU_DEPTH + 1), slot_next = ring(z0 + 1), slot_cur = ring(z0);  // rotate with z
   auto advance = [](int s) { return s + 1 == NR ? 0 : s + 1; };
   for (int z = z0; z < z1; ++z) {
     // plane z+1 has landed for every thread; the slot of plane z-2 is free
@@ -203,14 +208,16 @@ __global__ void __launch_bounds__(MX *MY) k_mu_z(const float *__restrict__ rho, 
     __syncthreads();
     issue(z + MU_DEPTH + 1, slot_in);
     dp = plane_sum(slot_next, cp);
+    const float m0 = s_m0[slot_cur][threadIdx.x];
     slot_in = advance(slot_in);
     slot_next = advance(slot_next);
+    slot_cur = advance(slot_cur);
     if (inside) {
-      const int n = x + kp.nx * y + nxy * z;
+      const int n = nxy0 + nxy * z;
       if (!(mask && mask[n])) {
         // lap = 6 sum_q w_q (rho(x + c_q) - rho(x)), split by planes
         const float lap = 6.0f * (w1(1) * (dm + (cm - c0)) + w1(0) * d0 + w1(1) * (dp + (cp - c0)));
-        mu[n] = mu0[n] - kp.kappa * lap;
+        mu[n] = m0 - kp.kappa * lap;
       }
     }
     dm = d0;
