@@ -492,15 +492,23 @@ void enqueue_segment(lbm_ctx *ctx, int n, char *pool, float *lam, float *lam_tmp
   const SegmentLayout L = segment_layout(ctx);
   auto slot = [&](int i) { return pool + (size_t)i * L.stride; };
   cudaStream_t s = ctx->stream;
+  // with the rest shift the shift bases of state i live in slot i: step i
+  // reads them from slot i-1 and writes them into slot i
+  float *const own_sb = ctx->fld.sb;
+  auto bases = [&](int i) { return (float *)(slot(i) + L.pops); };
   // recompute: step i reads slot i-1, writes slot i and captures the fields
   // of state i-1 into slot i-1
   for (int i = 1; i < n; ++i) {
     ctx->f[ctx->cur] = slot(i - 1);
     ctx->f[1 - ctx->cur] = slot(i);
     ctx->capture = (float *)(slot(i - 1) + L.cap_off);
+    if (L.rest) {
+      ctx->fld.sb = bases(i - 1);
+      ctx->sb_out = bases(i);
+    }
     launch_step(ctx);
     ctx->capture = nullptr;
-    if (L.rest) cudaMemcpyAsync(slot(i) + L.pops, ctx->fld.sb, L.sbb, cudaMemcpyDeviceToDevice, s);
+    ctx->sb_out = nullptr;
   }
   // adjoint steps from t0+n-1 down to t0, lambda ping-pong; the last state
   // of the segment was not stepped, so its fields are recomputed
@@ -510,8 +518,9 @@ void enqueue_segment(lbm_ctx *ctx, int n, char *pool, float *lam, float *lam_tmp
     ctx->f[ctx->cur] = slot(k);
     cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
     if (k == n - 1) {
-      if (L.rest) cudaMemcpyAsync(ctx->fld.sb, slot(k) + L.pops, L.sbb, cudaMemcpyDeviceToDevice, s);
+      if (L.rest) ctx->fld.sb = bases(k);
       launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout);
+      ctx->fld.sb = own_sb;
     } else {
       launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout, (const float *)(slot(k) + L.cap_off),
                           L.rest ? (const float *)(slot(k) + L.pops) : ctx->fld.sb);
@@ -582,8 +591,7 @@ int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool,
   char *pool = (char *)state_pool;
   cudaStream_t s = ctx->stream;
   cudaGetLastError();
-  cudaMemcpyAsync(pool, ckpt, L.sbytes, cudaMemcpyDeviceToDevice, s);
-  if (L.rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + L.pops, L.sbb, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(pool, ckpt, L.sbytes, cudaMemcpyDeviceToDevice, s);  // state and shift bases into slot 0
   void *own0 = ctx->f[0], *own1 = ctx->f[1];
   const int own_cur = ctx->cur;
   // one graph launch per segment (per-kernel profiling needs the launches)

@@ -110,6 +110,7 @@ struct lbm_ctx {
   void *f[2];
   int cur;
   float *capture;       // when set, the fused step writes rho, mu', u, F, Q of its input state here (11 N floats)
+  float *sb_out;        // when set, the fused step writes the new shift bases here instead of over fld.sb
   const float *wall_u;  // caller's 3 N wall velocities (read at solid nodes), or null: walls at rest
   lbm::Fields fld;
   double *red_partial;  // RED_BLOCKS * 2

@@ -283,12 +283,14 @@ template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return _
 // walls move (wall_u holds the solid nodes' velocities); compiled out of the
 // resting-wall instantiations, whose registers it would raise.  UNIT: every
 // rate but omega_1 is 1, so the collision reads only seven central moments
-// (to_central_unit, collide_cm_unit).
+// (to_central_unit, collide_cm_unit).  sb holds the shift bases of the input
+// state, sb_out receives those of the output state; they may be one array
+// (each node reads its own bases before it writes them).
 template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT>
 __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
-            float *__restrict__ sb, int *__restrict__ status, float *__restrict__ cap,
+            const float *sb, float *sb_out, int *__restrict__ status, float *__restrict__ cap,
             const float *__restrict__ wall_u, KParams kp, int TZ,
             const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -619,8 +621,8 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       }
     }
     if (rest) {
-      sb[n] = r_own;
-      sb[N + n] = c_own;
+      sb_out[n] = r_own;
+      sb_out[N + n] = c_own;
     }
   }
 }
@@ -755,7 +757,8 @@ void launch_fused_u(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map)
   const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
   const int tz = z_chunk(xyb, kp.nz, resident_slots<K>(NT, sm), 2);
   const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
-  K<<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j, d.mu, d.sb, ctx->status,
+  K<<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j, d.mu, d.sb,
+                                   ctx->sb_out ? ctx->sb_out : d.sb, ctx->status,
                                    ctx->capture, WALLV ? ctx->wall_u : nullptr, kp, tz, map);
 }
 
