@@ -283,10 +283,12 @@ template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return _
 // walls move (wall_u holds the solid nodes' velocities); compiled out of the
 // resting-wall instantiations, whose registers it would raise.  UNIT: every
 // rate but omega_1 is 1, so the collision reads only seven central moments
-// (to_central_unit, collide_cm_unit).  sb holds the shift bases of the input
+// (to_central_unit, collide_cm_unit).  REST: the populations are stored with
+// the destination-keyed rest shift (otherwise with the constant one), fixed
+// per launch so the shift choice costs no branches.  sb holds the shift bases of the input
 // state, sb_out receives those of the output state; they may be one array
 // (each node reads its own bases before it writes them).
-template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT>
+template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT, bool REST>
 __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
   const int nxy = nx * ny;
   const size_t N = (size_t)kp.N;
-  const bool rest = kp.shift_mode == LBM_SHIFT_REST;
+  constexpr bool rest = REST;
 
   if (TMA) {
     // the first plane's copy is in flight while the field planes load
@@ -747,12 +749,12 @@ const CUtensorMap *population_tmap(lbm_ctx *ctx, const void *p) {
   return e.ok ? &e.map : nullptr;
 }
 
-template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT>
+template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT, bool REST>
 void launch_fused_u(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
   const KParams &kp = ctx->kp;
   const Fields &d = ctx->fld;
   constexpr size_t sm = fused_smem_size<T>(TMA);
-  constexpr auto K = k_fused<T, MASK, TMA, WALLV, UNIT>;
+  constexpr auto K = k_fused<T, MASK, TMA, WALLV, UNIT, REST>;
   ensure_smem<K>(sm);
   const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
   const int tz = z_chunk(xyb, kp.nz, resident_slots<K>(NT, sm), 2);
@@ -771,10 +773,15 @@ bool unit_rates(const KParams &kp) {
 
 template <typename T, bool MASK, bool TMA, bool WALLV>
 void launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
-  if (unit_rates(ctx->kp))
-    launch_fused_u<T, MASK, TMA, WALLV, true>(ctx, fin, fout, map);
+  const bool unit = unit_rates(ctx->kp), rest = ctx->kp.shift_mode == LBM_SHIFT_REST;
+  if (unit && rest)
+    launch_fused_u<T, MASK, TMA, WALLV, true, true>(ctx, fin, fout, map);
+  else if (unit)
+    launch_fused_u<T, MASK, TMA, WALLV, true, false>(ctx, fin, fout, map);
+  else if (rest)
+    launch_fused_u<T, MASK, TMA, WALLV, false, true>(ctx, fin, fout, map);
   else
-    launch_fused_u<T, MASK, TMA, WALLV, false>(ctx, fin, fout, map);
+    launch_fused_u<T, MASK, TMA, WALLV, false, false>(ctx, fin, fout, map);
 }
 
 template <typename T>
