@@ -311,6 +311,25 @@ __device__ __forceinline__ Site site_of(const KParams &kp) {
   return s;
 }
 
+// Site of node n (for kernels over node lists)
+__device__ __forceinline__ Site site_at(int n, const KParams &kp) {
+  Site s;
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz, nxy = nx * ny;
+  const int x = n % nx, t = n / nx, y = t % ny, z = t / ny;
+  s.in = true;
+  s.n = n;
+  s.ox[0] = x == 0 ? nx - 1 : -1;
+  s.ox[1] = 0;
+  s.ox[2] = x == nx - 1 ? -(nx - 1) : 1;
+  s.oy[0] = y == 0 ? (ny - 1) * nx : -nx;
+  s.oy[1] = 0;
+  s.oy[2] = y == ny - 1 ? -(ny - 1) * nx : nx;
+  s.oz[0] = z == 0 ? (nz - 1) * nxy : -nxy;
+  s.oz[1] = 0;
+  s.oz[2] = z == nz - 1 ? -(nz - 1) * nxy : nxy;
+  return s;
+}
+
 __device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
 // Block sums of M FP32 per-node values, added to the parameter slots
@@ -560,31 +579,35 @@ __global__ void __launch_bounds__(256) k_adj_mu(const uint8_t *__restrict__ mask
     if (cz_of(q)) v += cz_of(q) * a.phi[2 * N + m];
     s += weight_of(q) * v;
   }
-  a.pm[n] = ((mask && mask[n]) ? 0.0f : a.mu[n]) + 3.0f * s;  // total lmu into a.pm
+  // total lmu: in place in a.mu on fluid nodes (each thread reads only its
+  // own entry), into a.pm on solid nodes for the wetting gather
+  if (mask && mask[n])
+    a.pm[n] = 3.0f * s;
+  else
+    a.mu[n] = a.mu[n] + 3.0f * s;
 }
 
 // Eq. 36 transposed: mu(b) = sum_q w_q s(b+c_q) mu(b+c_q) / den(b) on solid
-// boundary nodes b.  Gathered at fluid nodes y: sum over the solid
-// neighbours b = y + c_p of (w_p / den(b)) lmu(b), with 1/den(b) stored per
-// node and the solid neighbours read from y's bitmask.
-__global__ void __launch_bounds__(256) k_adj_wet_mu(const uint8_t *__restrict__ mask,
+// boundary nodes b.  Gathered at the fluid nodes y next to walls (list fw of
+// n_fw nodes): sum over the solid neighbours b = y + c_p of (w_p / den(b))
+// lmu(b), with 1/den(b) stored per node and the solid neighbours read from
+// y's bitmask; added to y's lmu in a.mu.
+__global__ void __launch_bounds__(256) k_adj_wet_mu(const int *__restrict__ fw, int n_fw,
                                                     const uint32_t *__restrict__ nbr,
                                                     const float *__restrict__ inv_den, AdjFields a, KParams kp) {
-  const Site st = site_of(kp);
-  if (!st.in) return;
-  const int n = st.n;
-  if (mask[n]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_fw) return;
+  const int n = fw[i];
+  const Site st = site_at(n, kp);
   const uint32_t solid = nbr[n];
   float add = 0.0f;
-  if (solid) {
 #pragma unroll
-    for (int p = 0; p < 27; ++p) {
-      if (p == 13 || !((solid >> p) & 1u)) continue;
-      const int b = st.at(cx_of(p), cy_of(p), cz_of(p));
-      add += weight_of(p) * inv_den[b] * a.pm[b];
-    }
+  for (int p = 0; p < 27; ++p) {
+    if (p == 13 || !((solid >> p) & 1u)) continue;
+    const int b = st.at(cx_of(p), cy_of(p), cz_of(p));
+    add += weight_of(p) * inv_den[b] * a.pm[b];
   }
-  a.mu[n] = a.pm[n] + add;  // final lmu on fluid nodes into a.mu
+  a.mu[n] = a.mu[n] + add;  // final lmu
 }
 
 // lambda_q(t)(n) += lrho + c_q . lj with lj = a.u(n): all 27 loads are
@@ -673,17 +696,17 @@ __global__ void __launch_bounds__(BLK) k_adj_rho(const uint8_t *__restrict__ mas
   block_partials(pg, slots, partial);
 }
 
-// lambda_q(t)(x) += lrho(x) + c_q . lj(x) at fluid nodes next to walls, with
-// part 2 of Eqs. 37-38 transposed: lrho(y) += sum over solid neighbours b of
-// w_q (dave(b)/den(b)) lrho(b) (stored in a.F by k_adj_rho)
-__global__ void __launch_bounds__(256) k_adj_out_wall(const uint8_t *__restrict__ mask,
+// lambda_q(t)(x) += lrho(x) + c_q . lj(x) at the fluid nodes next to walls
+// (list fw), with part 2 of Eqs. 37-38 transposed: lrho(y) += sum over solid
+// neighbours b of w_q (dave(b)/den(b)) lrho(b) (stored in a.F by k_adj_rho)
+__global__ void __launch_bounds__(256) k_adj_out_wall(const int *__restrict__ fw, int n_fw,
                                                       const uint32_t *__restrict__ nbr, AdjFields a,
                                                       float *__restrict__ lam_t, KParams kp) {
-  const Site st = site_of(kp);
-  if (!st.in) return;
-  const int n = st.n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_fw) return;
+  const int n = fw[i];
+  const Site st = site_at(n, kp);
   const uint32_t solid = nbr[n];
-  if (mask[n] || solid == 0u) return;
   const size_t N = (size_t)kp.N;
   float lr = a.phi[n];
 #pragma unroll
@@ -890,8 +913,9 @@ void adj_tail(lbm_ctx *ctx, const float *lmu, const Regions &R, const Fields &d,
   k_adj_rho<<<grid3(ctx, ADJ_BY), dim3(32, ADJ_BY), 0, s>>>(ctx->mask, ctx->nbr, ctx->inv_den, d, ctx->adj, lmu,
                                                             lam_t, R.rho, kp);
   ctx->launches++;
-  if (lam_t && ctx->n_bnd) {
-    k_adj_out_wall<<<grid3(ctx, 8), dim3(32, 8), 0, s>>>(ctx->mask, ctx->nbr, ctx->adj, lam_t, kp);
+  if (lam_t && ctx->n_fw) {
+    k_adj_out_wall<<<(ctx->n_fw + 255) / 256, 256, 0, s>>>(ctx->bnd + ctx->n_bnd, ctx->n_fw, ctx->nbr, ctx->adj,
+                                                          lam_t, kp);
     ctx->launches++;
   }
 }
@@ -901,9 +925,11 @@ const float *adj_mu(lbm_ctx *ctx) {
   const KParams &kp = ctx->kp;
   k_adj_mu<<<grid3(ctx, 8), dim3(32, 8), 0, ctx->stream>>>(ctx->mask, ctx->adj, kp);
   ctx->launches++;
-  if (!ctx->mask) return ctx->adj.pm;
-  k_adj_wet_mu<<<grid3(ctx, 8), dim3(32, 8), 0, ctx->stream>>>(ctx->mask, ctx->nbr, ctx->inv_den, ctx->adj, kp);
-  ctx->launches++;
+  if (ctx->n_fw) {
+    k_adj_wet_mu<<<(ctx->n_fw + 255) / 256, 256, 0, ctx->stream>>>(ctx->bnd + ctx->n_bnd, ctx->n_fw, ctx->nbr,
+                                                                  ctx->inv_den, ctx->adj, kp);
+    ctx->launches++;
+  }
   return ctx->adj.mu;
 }
 

@@ -184,6 +184,7 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
   cudaMemsetAsync(ctx->f[1], 0, L.f1 - L.f0, ctx->stream);
   cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), ctx->stream);
   ctx->n_bnd = 0;
+  ctx->n_fw = 0;
   if (solid_mask) {
     launch_mark_boundary(ctx);
     int cnt = 0;
@@ -194,6 +195,16 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
       return rc == LBM_OK ? LBM_ERR_CUDA : rc;
     }
     ctx->n_bnd = cnt;
+    if (cnt) {  // the adjoint's list of fluid nodes next to walls, after the solid one
+      launch_mark_fluid_wall(ctx);
+      cudaMemcpyAsync(&cnt, ctx->status + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+      if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        int rc = check_cuda(ctx, "fluid wall list");
+        delete ctx;
+        return rc == LBM_OK ? LBM_ERR_CUDA : rc;
+      }
+      ctx->n_fw = cnt;
+    }
   }
   if (check_cuda(ctx, "lbm_init_domain") != LBM_OK) {
     delete ctx;

@@ -304,19 +304,40 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_counts(int *__restrict__ counts
   if (t == SCAN_T - 1) *total = part[t];
 }
 
-__global__ void __launch_bounds__(BLOCK) k_write_bnd(const float *__restrict__ inv_den, const int *__restrict__ offsets,
-                                                     int *__restrict__ bnd, KParams kp) {
-  __shared__ int warp_base[BLOCK / 32];
+// per-block counts of fluid nodes with a solid neighbour (second list)
+__global__ void __launch_bounds__(BLOCK) k_count_fw(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
+                                                    int *__restrict__ counts, KParams kp) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool boundary = n < kp.N && inv_den[n] > 0.0f;
-  const unsigned ball = __ballot_sync(0xffffffffu, boundary);
+  const bool fw = n < kp.N && !mask[n] && nbr[n] != 0u;
+  const int c = __syncthreads_count(fw);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// writes the nodes of a block that satisfy `in` at out[offsets[block] + rank]
+__device__ __forceinline__ void compact_block(bool in, int n, const int *__restrict__ offsets, int *__restrict__ out) {
+  __shared__ int warp_base[BLOCK / 32];
+  const unsigned ball = __ballot_sync(0xffffffffu, in);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) warp_base[w] = __popc(ball);
   __syncthreads();
   int base = offsets[blockIdx.x];
   for (int i = 0; i < w; ++i) base += warp_base[i];
-  if (boundary) bnd[base + __popc(ball & ((1u << lane) - 1u))] = n;
+  if (in) out[base + __popc(ball & ((1u << lane) - 1u))] = n;
 }
+
+__global__ void __launch_bounds__(BLOCK) k_write_fw(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
+                                                    const int *__restrict__ offsets, int *__restrict__ list,
+                                                    KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  compact_block(n < kp.N && !mask[n] && nbr[n] != 0u, n, offsets, list);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_write_bnd(const float *__restrict__ inv_den, const int *__restrict__ offsets,
+                                                     int *__restrict__ bnd, KParams kp) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  compact_block(n < kp.N && inv_den[n] > 0.0f, n, offsets, bnd);
+}
+
 
 template <typename T>
 __global__ void __launch_bounds__(BLOCK) k_get_pop(const T *__restrict__ f, const uint8_t *__restrict__ mask,
@@ -437,6 +458,14 @@ void launch_mark_boundary(lbm_ctx *ctx) {
   k_mark_nbr<<<g, BLOCK, 0, ctx->stream>>>(ctx->mask, ctx->nbr, ctx->inv_den, ctx->scan, ctx->kp);
   k_scan_counts<<<1, SCAN_T, 0, ctx->stream>>>(ctx->scan, g, ctx->status + 1);
   k_write_bnd<<<g, BLOCK, 0, ctx->stream>>>(ctx->inv_den, ctx->scan, ctx->bnd, ctx->kp);
+  ctx->launches += 3;
+}
+
+void launch_mark_fluid_wall(lbm_ctx *ctx) {
+  const int g = blocks_for(ctx->N);
+  k_count_fw<<<g, BLOCK, 0, ctx->stream>>>(ctx->mask, ctx->nbr, ctx->scan, ctx->kp);
+  k_scan_counts<<<1, SCAN_T, 0, ctx->stream>>>(ctx->scan, g, ctx->status + 1);
+  k_write_fw<<<g, BLOCK, 0, ctx->stream>>>(ctx->mask, ctx->nbr, ctx->scan, ctx->bnd + ctx->n_bnd, ctx->kp);
   ctx->launches += 3;
 }
 

@@ -103,7 +103,9 @@ struct lbm_ctx {
   cudaStream_t stream;
   const uint8_t *mask;  // device, may be null
   int n_bnd;
-  int *bnd;             // solid nodes with at least one fluid neighbour, in node order
+  int *bnd;             // solid nodes with at least one fluid neighbour, in node order; then, from
+                        // bnd + n_bnd, the n_fw fluid nodes with a solid neighbour (adjoint only)
+  int n_fw;
   uint32_t *nbr;        // per node: bit q set when node + c_q is solid (walls only)
   float *inv_den;       // per solid boundary node: 1 / sum of w_q over fluid neighbours, else 0
   int *scan;            // per-block counts of the boundary-list compaction
@@ -157,6 +159,7 @@ constexpr int STATUS_TIMEOUT = 4;
 // Launchers (lbm_forward.cu).  Each enqueues on ctx->stream and counts its
 // launches; they do not check errors (the caller does).
 void launch_mark_boundary(lbm_ctx *ctx);
+void launch_mark_fluid_wall(lbm_ctx *ctx);  // after n_bnd is known; total into status[1]
 void launch_step(lbm_ctx *ctx);                 // one full time step, swaps buffers
 void launch_step_fused(lbm_ctx *ctx);           // the three-kernel step (lbm_step_fused.cu)
 void launch_wet_rho(lbm_ctx *ctx);
