@@ -18,9 +18,12 @@
  *    Population arrays are 27*N elements, population q at offset q*N.
  *  - Memory: the caller owns every buffer.  Device pointers are plain CUDA
  *    device addresses on the current device; host pointers are ordinary host
- *    memory.  The library never allocates device memory: all of its device
+ *    memory.  The library allocates no device buffers: all of its device
  *    state lives in the caller's workspace, and the context keeps views of it
- *    (and of the solid mask) until lbm_destroy.
+ *    (and of the solid mask) until lbm_destroy.  The CUDA graphs that
+ *    lbm_step and lbm_adjoint_segment capture hold driver-managed resources,
+ *    and one private stream is created to capture them; lbm_destroy releases
+ *    both.
  *  - Streams: all device work of a context is enqueued on the stream given at
  *    lbm_init_domain (NULL = legacy default stream).  Entry points return after
  *    enqueueing unless documented otherwise.
