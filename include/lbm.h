@@ -184,6 +184,13 @@ int lbm_step(lbm_ctx *ctx, int n);
  * stay set until lbm_set_state / lbm_set_raw_state / lbm_set_populations). */
 int lbm_sync_status(lbm_ctx *ctx);
 
+/* Enqueue a copy of the device status word into host memory *dst (pinned
+ * memory for an asynchronous copy) and return without waiting: after the
+ * stream reaches it, *dst is 0 when no flag is set and nonzero otherwise
+ * (lbm_sync_status then returns the error code).  Lets a caller read each
+ * step's status while the next step runs.  LBM_ERR_ARG for a null pointer. */
+int lbm_status_async(lbm_ctx *ctx, int *dst);
+
 /*
  * Macroscopic fields of the current state (Eq. 11 and Eq. 2): rho (N floats,
  * wetting value on solid nodes next to fluid), u (3*N floats, force-corrected

@@ -35,6 +35,7 @@ SIGNATURES = {
     "lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_sync_status": (C.c_int, [C.c_void_p]),
+    "lbm_status_async": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_moments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_state_bytes": (C.c_size_t, [C.c_void_p]),
     "lbm_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -247,6 +248,16 @@ class Domain:
 
     def sync_status(self) -> int:
         return self.lib.lbm_sync_status(self.ctx)
+
+    def status_async(self, out):
+        """Enqueue a copy of the status word into `out` (a pinned int32 CPU
+        tensor with at least one element) and return at once; once the stream
+        has reached it, out[0] != 0 means a flag is set (sync_status gives the
+        code)."""
+        t = self.torch
+        if out.device.type != "cpu" or out.dtype != t.int32 or out.numel() < 1:
+            raise ValueError("status_async needs an int32 CPU tensor")
+        self._check(self.lib.lbm_status_async(self.ctx, C.c_void_p(out.data_ptr())), "lbm_status_async")
 
     def moments(self) -> dict:
         t = self.torch

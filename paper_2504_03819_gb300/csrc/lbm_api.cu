@@ -379,6 +379,13 @@ int lbm_sync_status(lbm_ctx *ctx) {
   return LBM_OK;
 }
 
+int lbm_status_async(lbm_ctx *ctx, int *dst) {
+  if (!ctx || !dst) return LBM_ERR_ARG;
+  cudaGetLastError();
+  cudaMemcpyAsync(dst, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  return check_cuda(ctx, "lbm_status_async");
+}
+
 int lbm_moments(lbm_ctx *ctx, float *rho, float *u, float *mu, double *mass_energy) {
   if (!ctx) return LBM_ERR_ARG;
   if (!ctx->have_state) return fail(ctx, LBM_ERR_STATE, "no state");

@@ -178,12 +178,17 @@ def test_status_flags():
     f = oracle_init(case).float()
     d.set_populations(f)
     d.step(2)
+    st = torch.full((2,), -1, dtype=torch.int32).pin_memory()
+    d.status_async(st[0:1])  # asynchronous read of the same word
     assert d.sync_status() == 0
+    assert int(st[0]) == 0
     bad = f.clone()
     bad[:, 3, 4, 5] = float("nan")
     d.set_populations(bad)
     d.step(1)
+    d.status_async(st[1:2])
     assert d.sync_status() == -4  # LBM_ERR_NONFINITE
+    assert int(st[1]) != 0
     big = f.clone()
     big[13, 2, 2, 2] = 20.0  # rho > 1/b = 10.5
     d.set_populations(big)
