@@ -296,7 +296,10 @@ size_t lbm_adjoint_pool_bytes(const lbm_ctx *ctx);
  * dJ/df(t0); lam_tmp: device, 27*N floats of scratch; grad_params:
  * accumulated as in lbm_adjoint_step.  The context's current state becomes
  * ckpt.  Equivalent to n calls of lbm_adjoint_step on the recomputed states
- * (up to FP32 rounding of the fields).  The sweep between the checkpoint
+ * (up to FP32 rounding of the fields).  The status word is cleared at the
+ * start, as by lbm_set_raw_state, and keeps every flag the recompute raises,
+ * so lbm_sync_status after the sweep reports a segment that left the EOS
+ * domain.  The sweep between the checkpoint
  * copy-in and the restore runs as one CUDA graph, captured at the first call
  * with a given n, state_pool, lam, lam_tmp and grad_params (the two most
  * recent are kept; lbm_set_params and lbm_set_wall_velocity discard them);

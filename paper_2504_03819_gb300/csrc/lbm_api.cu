@@ -534,7 +534,6 @@ void enqueue_segment(lbm_ctx *ctx, int n, char *pool, float *lam, float *lam_tmp
   launch_adjoint_partials_zero(ctx);  // the segment's gradient partials accumulate over its steps
   for (int k = n - 1; k >= 0; --k) {
     ctx->f[ctx->cur] = slot(k);
-    cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
     if (k == n - 1) {
       if (L.rest) ctx->fld.sb = bases(k);
       launch_adjoint_step(ctx, ctx->f[ctx->cur], lin, lout);
@@ -610,6 +609,9 @@ int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool,
   cudaStream_t s = ctx->stream;
   cudaGetLastError();
   cudaMemcpyAsync(pool, ckpt, L.sbytes, cudaMemcpyDeviceToDevice, s);  // state and shift bases into slot 0
+  // the status word starts clear, as after lbm_set_raw_state, and keeps any
+  // flag the recompute raises for lbm_sync_status after the sweep
+  cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
   void *own0 = ctx->f[0], *own1 = ctx->f[1];
   const int own_cur = ctx->cur;
   // one graph launch per segment (per-kernel profiling needs the launches)
