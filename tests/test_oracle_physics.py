@@ -214,3 +214,38 @@ def test_shear_wave_decays_at_the_model_viscosity(mode):
     a2 = amplitude(f)
     rate = math.log(a1 / a2) / 300.0
     assert rate == pytest.approx(nu * k * k, rel=0.02)
+
+
+def test_sound_wave_frequency_follows_the_eos_and_capillarity():
+    """Sec. II: the force F = (1/3 - rho) grad mu with the pressure p_m of the
+    generalized equilibrium leaves -rho grad mu in the momentum equation, so a
+    small density wave rho_l (1 + eps cos kz) in the liquid oscillates at
+    omega^2 = k^2 rho (mu0'(rho) + kappa lambda_k), with lambda_k = 2(1 - cos k)
+    the eigenvalue of minus the lattice Laplacian (Eq. 2) and mu0' of the vdW
+    EOS (Eq. 32).  On the lattice k becomes sin k, the eigenvalue of the
+    model's gradient stencil for this mode (O(k^2) dispersion).  At 0.7 T_c,
+    kappa = 0.02 on 1 x 1 x 32 nodes the period is 61.8 steps; the capillary
+    term moves omega by 1 %, and a pressure of rho / 3 instead would move it
+    by 11 %.  The period from interpolated zero crossings of the mode
+    amplitude over six periods is held to 0.3 % (measured +0.12 %; +0.03 % on
+    64 nodes, where the k form is off by -0.13 % against -0.52 % on 32)."""
+    eos, p, rl, rv = setup()
+    nz, eps = 32, 1e-5
+    solid = torch.zeros(nz, 1, 1, dtype=torch.bool)
+    k = 2.0 * math.pi / nz
+    z = torch.arange(nz, dtype=torch.float64)
+    rho0 = (rl * (1.0 + eps * torch.cos(k * z))).view(nz, 1, 1)
+    h = 1e-6
+    dmu0 = (eos.mu0(rl + h) - eos.mu0(rl - h)) / (2.0 * h)
+    omega = math.sin(k) * math.sqrt(rl * (dmu0 + p.kappa * 2.0 * (1.0 - math.cos(k))))
+    f = S.initial_populations(rho0, None, solid, p)
+    amp = []
+    for _ in range(400):
+        r = S.macroscopic(f, solid, p)["rho"][:, 0, 0]
+        amp.append(float(((r - r.mean()) * torch.cos(k * z)).sum()))
+        f = S.step(f, solid, p)
+    cross = [i - 1 + amp[i - 1] / (amp[i - 1] - amp[i]) for i in range(1, len(amp))
+             if (amp[i - 1] > 0.0) != (amp[i] > 0.0)]
+    period = 2.0 * (cross[-1] - cross[0]) / (len(cross) - 1)
+    assert len(cross) >= 12
+    assert 2.0 * math.pi / period == pytest.approx(omega, rel=0.003)
