@@ -1,0 +1,31 @@
+"""Scaled copies of the paper-shaped workloads for the 1000-step parity runs.
+
+Plain data shared by the script that writes the FP64 oracle's results
+(make_long_parity.py, which calls only oracle/ and the input generator) and
+by the GPU test that compares the CUDA library with them.  Each copy keeps
+the workload's model parameters and shrinks the domain so the oracle finishes
+1000 steps in minutes:
+
+  droplet24   stationary droplet (64^3, R = 8 workload): 24^3 periodic, R = 8,
+              interface width 5, u = 0
+  moving24    moving droplet (256^3, R = 32, U = (0.05, 0.02, 0), omega_1 =
+              1.6 workload): 24^3 periodic, R = 6, width 2 (width 5 diverges
+              with this EOS), same U and rates
+  wall32      droplet on a wall (256 x 256 x 128, R = 40, phi-wetting
+              workload): 32 x 32 x 16 with solid planes z = 0 and z = 15,
+              hemisphere R = 5 on the wall plane z = 0.5, width 2, phi = 1.2
+
+All: van der Waals a = 9/49, b = 2/21, R = 1 at T = 0.85 T_c, kappa = 0.01.
+"""
+
+STEPS = 1000
+
+LONG_CASES = {
+    "droplet24": dict(n=(24, 24, 24), radius=8.0, width=5.0, u=(0.0, 0.0, 0.0), walls=(),
+                      omega1=1.0, wetting_mode=0, wetting_value=0.0),
+    "moving24": dict(n=(24, 24, 24), radius=6.0, width=2.0, u=(0.05, 0.02, 0.0), walls=(),
+                     omega1=1.6, wetting_mode=0, wetting_value=0.0),
+    "wall32": dict(n=(32, 32, 16), radius=5.0, width=2.0, u=(0.0, 0.0, 0.0), walls=(0, 15),
+                   omega1=1.0, wetting_mode=1, wetting_value=1.2),
+}
+EOS = dict(a=9.0 / 49.0, b=2.0 / 21.0, R=1.0, t_over_tc=0.85, kappa=0.01)
