@@ -3,9 +3,18 @@
 One "step" is one full time step of the hot path (moments, wetting, chemical
 potential, force, corrections, central-moment collision, streaming) over the
 whole domain.  Default workload: the moving-droplet case -- 256^3 periodic,
-droplet R = 32 (tanh width 5), uniform initial velocity (0.05, 0.02, 0),
-van der Waals a = 9/49, b = 2/21, R = 1 at T = 0.85 T_c, kappa = 0.01,
-omega_1 = 1.6 and all other rates 1, FP32 population storage.
+droplet R = 32 (tanh width 2: width 5 diverges with this EOS), uniform
+initial velocity (0.05, 0.02, 0), van der Waals a = 9/49, b = 2/21, R = 1 at
+T = 0.85 T_c, kappa = 0.01, omega_1 = 1.6 and all other rates 1, FP32
+population storage.
+
+Timing: the headline runs the production path (lbm_step(n): CUDA graphs,
+per-kernel profiling off), REPEATS regions of exactly K steps each bracketed
+by a barrier and synchronize on both sides, CUDA events on the library's
+stream; value = the median region (best also reported).  A sustained region
+of about one second follows for the clock record.  The per-kernel shares and
+the roofline come from a separate profiled pass (direct launches, CUDA events
+around each kernel).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -40,7 +49,7 @@ WORKLOAD_NAME = ("moving droplet 256^3 periodic, R=32 (tanh width 2), U=(0.05,0.
 # `--profile-case step128` (k_fused<float>, 128^3, 2,097,152 nodes): 289.42 MB
 # read + 194.78 MB written = 230.9 B per node, scaled by 8 to one 256^3 launch
 # (the kernel's traffic is proportional to the nodes it updates).
-NCU_TRAFFIC = {"f32": {"bytes_per_launch": 3873570816, "bytes_per_lu": 230.9,
+NCU_TRAFFIC = {"f32": {"kernel": "collide", "bytes_per_launch": 3873570816, "bytes_per_lu": 230.9,
                        "captured_on": "128^3, scaled x8", "src": "776652518277dd28"}}
 
 
@@ -150,29 +159,44 @@ def barrier(world: int):
         dist.barrier()
 
 
-def time_device_steps(dom, steps: int, warmup: int, world: int, profile: bool):
-    """W untimed steps, then exactly K steps between barrier + synchronize on
-    both sides, timed with CUDA events on the library's stream."""
+REPEATS = 5            # timed regions of K steps on the production path
+SUSTAIN_S = 1.0        # seconds of the sustained region (clock record)
+
+
+def time_regions(dom, steps: int, repeats: int, world: int):
+    """Production path (lbm_step(n): CUDA graphs, profiling off): `repeats`
+    regions of exactly `steps` steps, each bracketed by a barrier and
+    synchronize on both sides and timed with CUDA events on the library's
+    stream.  Returns the per-region times (ms) and the kernel launches of one
+    region."""
     import torch
-    dom.step(warmup)
+    ms, launches = [], 0
+    for _ in range(repeats):
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        n0 = dom.launch_count()
+        start.record(dom.stream)
+        dom.step(steps)
+        stop.record(dom.stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms.append(start.elapsed_time(stop))
+        launches = dom.launch_count() - n0
+    return ms, launches
+
+
+def time_profiled(dom, steps: int):
+    """Per-kernel CUDA-event times over `steps` directly launched steps (the
+    profiled pass: graphs off); {name: (total ms, launches)}."""
+    import torch
     torch.cuda.synchronize()
-    if profile:
-        dom.profile(True)
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    torch.cuda.synchronize()
-    n0 = dom.launch_count()
-    start.record(dom.stream)
+    dom.profile(True)
     dom.step(steps)
-    stop.record(dom.stream)
     torch.cuda.synchronize()
-    barrier(world)
-    ms = start.elapsed_time(stop)
-    launches = dom.launch_count() - n0
-    prof = dom.profile_read() if profile else None
-    if profile:
-        dom.profile(False)
-    return ms, launches, prof
+    prof = dom.profile_read()
+    dom.profile(False)
+    return prof
 
 
 def run_ours(args, world, rank, local):
@@ -189,18 +213,29 @@ def run_ours(args, world, rank, local):
         dom = Domain(nx, ny, nz, storage, device=f"cuda:{local}")
         dom.set_params(p)
         dom.set_state(torch.from_numpy(rho0), torch.from_numpy(u0))
-        sampler = ClockSampler(local) if storage == "f32" else None
-        ms, launches, prof = time_device_steps(dom, args.steps, args.warmup, world, profile=True)
-        clocks = sampler.stop() if sampler else None
+        dom.step(args.warmup)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        ms, launches = time_regions(dom, args.steps, REPEATS, world)
+        ms = [max_over_ranks(v, world) for v in ms]
+        med = statistics.median(ms)
+        # sustained region of about --sustain-s seconds for the clock record
+        n_sus = max(args.steps, int(math.ceil(args.sustain_s / (med / args.steps * 1e-3)))) if args.sustain_s > 0 else 0
+        sus = time_regions(dom, n_sus, 1, world)[0] if n_sus else [float("nan")]
+        clocks = sampler.stop()
         status = dom.sync_status()
-        ms_max = max_over_ranks(ms, world)
-        mlups = world * N * args.steps / (ms_max * 1e-3) / 1e6
-        coll_ms, coll_n = prof["collide"]
-        coll_avg = coll_ms / max(coll_n, 1)
-        achieved = ALG_BYTES[storage] * N / (coll_avg * 1e-3) / 1e9
+        prof = time_profiled(dom, min(args.steps, 50) if args.steps >= 8 else args.steps)
+        status = status or dom.sync_status()
+        mlups = world * N * args.steps / (med * 1e-3) / 1e6
+        top = max(prof, key=lambda k: prof[k][0])
+        top_ms, top_n = prof[top]
+        top_avg = top_ms / max(top_n, 1)
+        achieved = ALG_BYTES[storage] * N / (top_avg * 1e-3) / 1e9
         total_prof = sum(v[0] for v in prof.values())
-        results[storage] = dict(ms=ms_max, mlups=mlups, launches=launches, status=status, clocks=clocks,
-                                collide_avg_ms=coll_avg, achieved=achieved, prof=prof, total_prof=total_prof)
+        results[storage] = dict(ms=med, ms_all=ms, best=min(ms), sustained_ms=max_over_ranks(sus[0], world),
+                                sustained_steps=max(n_sus, 1), mlups=mlups, launches=launches, status=status,
+                                clocks=clocks, top=top, top_avg_ms=top_avg, achieved=achieved, prof=prof,
+                                total_prof=total_prof, prof_steps=min(args.steps, 50) if args.steps >= 8 else args.steps)
         del dom
         torch.cuda.empty_cache()
 
@@ -244,11 +279,6 @@ def run_ours(args, world, rank, local):
     e2e = {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "status_ok": not bad}
     return results, e2e, peak, peak_src, N
-
-
-ADJ_WORKLOAD = ("differentiable droplet on a wall 64^3 (solid planes z=0, z=63), hemisphere R=16 + N(0,1e-3) "
-                "noise (default_rng(12345)), vdW a=9/392 b=2/21 T=0.85Tc kappa=0.02 (the stated a=9/49, "
-                "kappa=0.01 diverges), phi-wetting 1.2, rates 1, contact-line radius objective")
 
 
 def run_configs(local, steps: int = 200):
@@ -299,10 +329,16 @@ def run_configs(local, steps: int = 200):
     return out
 
 
-def run_adjoint(args, local):
-    """Forward time of `adjoint_steps` steps against the time of the full
-    adjoint sweep (segment recompute from checkpoints every 100 steps,
-    adjoint steps, initialisation adjoint), both on the library stream."""
+ADJ_WORKLOAD = ("differentiable droplet on a wall {n}^3 (solid planes z=0, z={top}), hemisphere R={r} + N(0,1e-3) "
+                "noise (default_rng(12345)), vdW a=9/392 b=2/21 T=0.85Tc kappa=0.02 (the stated a=9/49, "
+                "kappa=0.01 diverges), phi-wetting 1.2, rates 1, contact-line radius objective")
+
+
+def run_adjoint(local, n: int, T: int, K: int = 100):
+    """Forward time of T steps against the time of the full adjoint sweep
+    (segment recompute from checkpoints every K steps, adjoint steps,
+    initialisation adjoint), both on the library stream, on the n^3 wall
+    workload (R = n/4)."""
     import numpy as np
     import torch
 
@@ -310,10 +346,9 @@ def run_adjoint(args, local):
     from paper_2504_03819_gb300 import binding as Bd
     from paper_2504_03819_gb300 import inputs as I
     from paper_2504_03819_gb300.adjoint import backward_from, forward_checkpoints
-    n, T, K = 64, args.adjoint_steps, 100
     p = Params.vdw(9.0 / 392.0, 2.0 / 21.0, 1.0, 0.85, 0.02, wetting_mode=Bd.WET_PHI, wetting_value=1.2)
     mask = I.wall_mask(n, n, n, planes=(0, n - 1))
-    rho0 = torch.from_numpy(I.add_noise(I.sessile_droplet(n, n, n, 16.0, p.rho_l, p.rho_v), 1e-3,
+    rho0 = torch.from_numpy(I.add_noise(I.sessile_droplet(n, n, n, n / 4.0, p.rho_l, p.rho_v), 1e-3,
                                         seed=12345).astype(np.float32))
     dom = Domain(n, n, n, "f32", solid_mask=mask, device=f"cuda:{local}")
     dom.set_params(p)
@@ -338,10 +373,15 @@ def run_adjoint(args, local):
     e1.record(dom.stream)
     torch.cuda.synchronize()
     t_bwd = e0.elapsed_time(e1)
-    return {"workload": ADJ_WORKLOAD, "steps": T, "checkpoint_every": K, "forward_ms_per_step": t_fwd / T,
-            "adjoint_ms_per_step": t_bwd / T, "ratio": t_bwd / t_fwd, "status": status,
-            "J": float(J[0]), "dJ_dwetting": float(grad[12]), "dJ_dkappa": float(grad[0]),
-            "dJ_drho0_maxabs": float(g_rho0.abs().max()), "launches_backward": dom.launch_count() - n0}
+    out = {"workload": ADJ_WORKLOAD.format(n=n, top=n - 1, r=n // 4), "nodes": n ** 3,
+           "state_MB": dom.state_bytes() / 1e6, "steps": T, "checkpoint_every": K,
+           "forward_ms_per_step": t_fwd / T, "adjoint_ms_per_step": t_bwd / T, "ratio": t_bwd / t_fwd,
+           "status": status, "J": float(J[0]), "dJ_dwetting": float(grad[12]), "dJ_dkappa": float(grad[0]),
+           "dJ_drho0_maxabs": float(g_rho0.abs().max()), "launches_backward": dom.launch_count() - n0}
+    dom.close()
+    del ckpts
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_sample(nx: int, ny: int, nz: int, nsteps: int):
@@ -370,6 +410,45 @@ def cpu_sample(nx: int, ny: int, nz: int, nsteps: int):
         f = S.step(f, solid, p)
     dt = time.perf_counter() - t0
     return nx * ny * nz * nsteps / dt / 1e6, torch.get_num_threads(), dt
+
+
+def cpu_model() -> str:
+    """CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline():
+    """The FP64 oracle as it stands on this host: all cores (6 steps on a
+    256 x 256 x 2 slab through the droplet centre) and one thread (3 steps on a
+    64 x 64 x 2 slab)."""
+    import torch
+    n_all = torch.get_num_threads()
+    mlups, cores, dt = cpu_sample(256, 256, 2, 6)
+    torch.set_num_threads(1)
+    try:
+        mlups1, _, dt1 = cpu_sample(64, 64, 2, 3)
+    finally:
+        torch.set_num_threads(n_all)
+    return {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"6 FP64 oracle steps on a 256x256x2 slab through the droplet centre ({dt:.1f} s)",
+            "one_thread": {"value": mlups1, "unit": "MLUPS", "cores": 1,
+                           "sample": f"3 FP64 oracle steps on a 64x64x2 slab ({dt1:.1f} s)"},
+            "cpu_model": cpu_model(), "host_cpus": os.cpu_count()}
 
 
 def profile_case(name: str):
@@ -420,6 +499,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the MLUPS of the other workload configurations")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--sustain-s", type=float, default=SUSTAIN_S,
+                    help="seconds of the sustained region after the repeats (0: none)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case)
@@ -448,37 +529,53 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     res, e2e, peak, peak_src, N = run_ours(args, world, rank, local)
-    adj = run_adjoint(args, local) if args.adjoint_steps > 0 else None
+    adj = None
+    if args.adjoint_steps > 0:
+        # 64^3 (state 30 MB: L2-resident) and 128^3 (243 MB: HBM-resident)
+        adj = {"64^3": run_adjoint(local, 64, args.adjoint_steps),
+               "128^3": run_adjoint(local, 128, min(args.adjoint_steps, 400))}
     configs = run_configs(local) if not args.no_configs else None
     if rank != 0:
         return
     r32, r16 = res["f32"], res["f16"]
     cpu = None
     if not args.no_cpu_baseline and world >= 1:
-        sx, sy, sz = 256, 256, 2
-        mlups, cores, dt = cpu_sample(sx, sy, sz, 6)
-        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"6 FP64 oracle steps on a {sx}x{sy}x{sz} slab through the droplet centre ({dt:.1f} s)"}
+        cpu = cpu_baseline()
     traffic = None
     t = NCU_TRAFFIC.get("f32")
-    if t and t["src"] == src_hash():
+    if t and t["src"] == src_hash() and t.get("kernel") == r32["top"]:
         traffic = t["bytes_per_launch"]
+
+    def per_step(r):
+        return {k: v[0] / r["prof_steps"] for k, v in r["prof"].items() if v[1]}
+
     line = {
         "metric": METRIC, "value": r32["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "storage": "f32", "nodes": N,
-                   "l2": "state 1.8 GB > L2 (inputs larger than L2, no flush)", "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "collide", "bound": "hbm", "achieved": r32["achieved"], "peak": peak,
+                   "l2": "state 1.8 GB > L2 (inputs larger than L2, no flush)", "parallelism": f"replicas x{world}",
+                   "path": "lbm_step(n), CUDA graphs, profiling off"},
+        "timing": {"repeats": REPEATS, "steps_per_region": args.steps,
+                   "median_ms_per_step": r32["ms"] / args.steps, "best_ms_per_step": r32["best"] / args.steps,
+                   "all_ms_per_step": [v / args.steps for v in r32["ms_all"]],
+                   "best_mlups": N * world * args.steps / (r32["best"] * 1e-3) / 1e6,
+                   "sustained": {"steps": r32["sustained_steps"],
+                                 "ms_per_step": r32["sustained_ms"] / r32["sustained_steps"]}},
+        "roofline": {"kernel": r32["top"], "bound": "hbm", "achieved": r32["achieved"], "peak": peak,
                      "unit": "GB/s", "frac": r32["achieved"] / peak, "peak_source": peak_src,
                      "traffic": traffic, "alg_bytes_per_lu": ALG_BYTES["f32"],
-                     "share_of_step": r32["prof"]["collide"][0] / r32["total_prof"]},
+                     "avg_launch_ms": r32["top_avg_ms"],
+                     "share_of_step": r32["prof"][r32["top"]][0] / r32["total_prof"]},
         "hbm_effective": {"bytes_per_lu": ALG_BYTES["f32"], "GB/s": r32["mlups"] * 1e6 * ALG_BYTES["f32"] / 1e9,
                           "frac": r32["mlups"] * 1e6 * ALG_BYTES["f32"] / 1e9 / peak, "peak_source": peak_src},
         "fp16_store": {"value": r16["mlups"], "unit": "MLUPS", "ms_per_step": r16["ms"] / args.steps,
+                       "best_ms_per_step": r16["best"] / args.steps,
+                       "vs_f32": r16["mlups"] / r32["mlups"],
                        "hbm_effective_frac": r16["mlups"] * 1e6 * ALG_BYTES["f16"] / 1e9 / peak,
-                       "collide_achieved_GBps": r16["achieved"], "status": r16["status"]},
-        "kernel_ms_per_step": {k: v[0] / max(v[1], 1) * (v[1] / args.steps) for k, v in r32["prof"].items() if v[1]},
+                       "top_kernel": r16["top"], "top_achieved_GBps": r16["achieved"],
+                       "kernel_ms_per_step": per_step(r16), "clocks": r16["clocks"], "status": r16["status"]},
+        "kernel_ms_per_step": per_step(r32),
         "adjoint": adj,
         "other_configs": configs,
         "e2e": e2e, "gpu_launches": r32["launches"], "clocks": r32["clocks"], "cpu_baseline": cpu,

@@ -179,10 +179,43 @@ int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0);
  */
 int lbm_step(lbm_ctx *ctx, int n);
 
+/*
+ * Step variant (off by default): with on = 1 the fused collision kernel also
+ * forms the moments of Eq. 11 (rho, j) and mu0(rho) of the state it writes,
+ * so the next step needs no separate pass over the 27 populations.  Blocks
+ * run in thread-block clusters spanning the x range and up to 16 blocks;
+ * after each plane a cluster barrier lets every block sum its nodes of the
+ * plane two behind (read back from L2), and a small pass completes the
+ * first and last row of each cluster and the first and last plane of each
+ * block's z range.  The moments are the bits of the separate pass, so the
+ * trajectory is bitwise the same either way.  It applies to domains whose
+ * population rows are whole multiples of 16 bytes (the tensor-copy path);
+ * others keep the separate pass.  On GB300 it is slower than the default
+ * (the 16-block clusters leave SMs of each GPC unused and the per-plane
+ * cluster barrier holds the blocks in step), so it is kept for measurement.
+ * on = 0 or 1, else LBM_ERR_ARG.
+ */
+int lbm_set_fused_moments(lbm_ctx *ctx, int on);
+
 /* Synchronise the context's stream and return LBM_OK, LBM_ERR_NONFINITE,
  * LBM_ERR_DOMAIN or LBM_ERR_TIMEOUT from the device status word (the flags
  * stay set until lbm_set_state / lbm_set_raw_state / lbm_set_populations). */
 int lbm_sync_status(lbm_ctx *ctx);
+
+/*
+ * Failure-path test hook (the paper has no counterpart).  In the next time
+ * step enqueued, one block of the fused collision kernel makes its first
+ * wait for a population tensor copy on a barrier that no thread arrives at,
+ * bounded by 1 ms instead of 2 s, so the wait runs out: the block then
+ * waits (with the full bound) for its own copy in flight, records
+ * LBM_ERR_TIMEOUT in the status word and returns, as a real late copy would
+ * make it do.  That step's populations are therefore incomplete.  One-shot;
+ * acts only on domains whose population rows are whole multiples of 16 bytes
+ * (nx a multiple of 4 with FP32 storage, of 8 with FP16), the ones staged by
+ * tensor copies.  Nothing faults, traps or hangs: lbm_sync_status returns
+ * LBM_ERR_TIMEOUT and lbm_set_state / lbm_set_raw_state clear it.
+ */
+int lbm_inject_wait_timeout(lbm_ctx *ctx);
 
 /* Enqueue a copy of the device status word into host memory *dst (pinned
  * memory for an asynchronous copy) and return without waiting: after the
@@ -311,6 +344,18 @@ int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool,
 
 /* ---- instrumentation ---------------------------------------------------- */
 
+/* Copy of the moments the next time step starts from, as stored (no
+ * recomputation): rho (N floats, fluid nodes; solid boundary nodes hold the
+ * last wetting value), j (3*N floats, sum f c, Eq. 11) and mu0 (N floats,
+ * mu0(rho) - mu_ref of the bulk chemical potential, Eq. 32), device
+ * pointers, each may be NULL.  A step whose fused kernel also produced the
+ * moments of its output leaves them stored; LBM_ERR_STATE when no valid
+ * moments are stored (after lbm_set_state, lbm_set_raw_state,
+ * lbm_set_populations or lbm_set_params, until the next step, and after
+ * steps that do not produce them).  For checking that path against a fresh
+ * moments pass (lbm_moments). */
+int lbm_stored_moments(lbm_ctx *ctx, float *rho, float *j, float *mu0);
+
 /* Number of kernels this context has launched since init. */
 long long lbm_launch_count(const lbm_ctx *ctx);
 
@@ -354,14 +399,20 @@ const char *lbm_kernel_name(int id);
  *  cuda_stream stream to enqueue on (NULL = default stream).
  * Returns LBM_ERR_SIZE if nx*ny*nz > LBM_NOALLOC_MAX_NODES, LBM_ERR_ARG for
  * invalid arguments (no message: there is no context), LBM_ERR_CUDA if a
- * CUDA call fails.  With a solid mask it synchronises the stream once (to
- * count boundary nodes).  Calls no cudaMalloc, cudaFree or allocating
- * library routine.
+ * CUDA call fails, and otherwise the step's status as lbm_sync_status
+ * reports it: LBM_ERR_NONFINITE / LBM_ERR_DOMAIN when a fluid density or
+ * momentum of f_in is non-finite or a density lies outside (0, 1/b) (f_out is
+ * then meaningless), else LBM_OK.  To read that status it synchronises the
+ * stream before returning, so the call is blocking (with a solid mask it
+ * also synchronises once earlier, to count boundary nodes).  Calls no
+ * cudaMalloc, cudaFree or allocating library routine.
  * The first call on each device looks up the device address of the static
- * array (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  Every call shares the one array, so calls
- * whose work overlaps on the GPU (different streams, threads or processes
- * sharing a context) race and give wrong results: serialise them.
+ * array (cudaGetSymbolAddress, with that device current) and keeps it for
+ * the process.  That address does not survive cudaDeviceReset or another
+ * teardown of the device's primary context: after one, do not call this
+ * entry point again in the same process.  Every call shares the one array,
+ * so calls whose work overlaps on the GPU (different streams, threads or
+ * processes sharing a context) race and give wrong results: serialise them.
  */
 int lbm_step_noalloc(const float *f_in, float *f_out, const uint8_t *solid_mask, int nx, int ny, int nz,
                      const lbm_params *params, void *cuda_stream);

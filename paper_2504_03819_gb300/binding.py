@@ -35,6 +35,9 @@ SIGNATURES = {
     "lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_sync_status": (C.c_int, [C.c_void_p]),
+    "lbm_inject_wait_timeout": (C.c_int, [C.c_void_p]),
+    "lbm_set_fused_moments": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_stored_moments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_status_async": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_moments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_state_bytes": (C.c_size_t, [C.c_void_p]),
@@ -248,6 +251,26 @@ class Domain:
 
     def sync_status(self) -> int:
         return self.lib.lbm_sync_status(self.ctx)
+
+    def fuse_moments(self, on: bool = True):
+        """Opt-in step variant: the fused kernel also forms the next state's
+        moments (lbm_set_fused_moments)."""
+        self._check(self.lib.lbm_set_fused_moments(self.ctx, 1 if on else 0), "lbm_set_fused_moments")
+
+    def stored_moments(self) -> dict:
+        """The moments the next step starts from, as stored (rho, j, mu0 - mu_ref;
+        lbm_stored_moments)."""
+        t = self.torch
+        rho = t.empty((self.nz, self.ny, self.nx), dtype=t.float32, device=self.device)
+        j = t.empty((3, self.nz, self.ny, self.nx), dtype=t.float32, device=self.device)
+        mu0 = t.empty_like(rho)
+        self._check(self.lib.lbm_stored_moments(self.ctx, _ptr(rho), _ptr(j), _ptr(mu0)), "lbm_stored_moments")
+        return {"rho": rho, "j": j, "mu0": mu0}
+
+    def inject_wait_timeout(self):
+        """Failure-path test hook: the next step's fused kernel lets one
+        bounded wait run out (lbm_inject_wait_timeout)."""
+        self._check(self.lib.lbm_inject_wait_timeout(self.ctx), "lbm_inject_wait_timeout")
 
     def status_async(self, out):
         """Enqueue a copy of the status word into `out` (a pinned int32 CPU

@@ -19,7 +19,8 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 // Workspace layout (each region 256-byte aligned):
 //   f[0], f[1]      27 N elements of the storage type each
-//   fields          rho N, j 3N, mu N, u 3N, F 3N, phi 3N, Q 3N, sb 2N, mu0 N floats
+//   fields          rho N, j 3N, mu N, u 3N, F 3N, phi 3N, Q 3N, sb 2N, mu0 N floats,
+//                   then the second moment set: rho N, j 3N, mu0 N floats
 //   boundary list   N ints
 //   neighbours      N uint32 solid-neighbour bitmasks, N floats of inverse
 //                   fluid-weight sums, N/256 + 2 ints of compaction counts
@@ -40,7 +41,7 @@ bool layout(int nx, int ny, int nz, int storage, Layout *L) {
   size_t off = 0;
   L->f0 = off; off = align_up(off + 27 * (size_t)N * elem);
   L->f1 = off; off = align_up(off + 27 * (size_t)N * elem);
-  L->fields = off; off = align_up(off + 20 * (size_t)N * sizeof(float));
+  L->fields = off; off = align_up(off + 25 * (size_t)N * sizeof(float));
   L->bnd = off; off = align_up(off + (size_t)N * sizeof(int));
   L->nbr = off; off = align_up(off + (size_t)N * sizeof(uint32_t));
   L->inv_den = off; off = align_up(off + (size_t)N * sizeof(float));
@@ -157,6 +158,9 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
   ctx->fld.Q = fl + 14 * N;
   ctx->fld.sb = fl + 17 * N;
   ctx->fld.mu0 = fl + 19 * N;
+  ctx->mom[0] = lbm::Moments{fl, fl + N, fl + 19 * N};
+  ctx->mom[1] = lbm::Moments{fl + 20 * N, fl + 21 * N, fl + 24 * N};
+  view_moments(ctx);
   ctx->bnd = (int *)(base + L.bnd);
   ctx->nbr = (uint32_t *)(base + L.nbr);
   ctx->inv_den = (float *)(base + L.inv_den);
@@ -178,7 +182,7 @@ int lbm_init_domain(lbm_ctx **out, int nx, int ny, int nz, int storage, const ui
   ctx->kp.nz = nz;
   ctx->kp.N = ctx->N;
   cudaGetLastError();
-  cudaMemsetAsync(ctx->fld.rho, 0, 20 * N * sizeof(float), ctx->stream);
+  cudaMemsetAsync(fl, 0, 25 * N * sizeof(float), ctx->stream);
   // solid-node population slots are never written by the step: start them at 0
   cudaMemsetAsync(ctx->f[0], 0, L.f1 - L.f0, ctx->stream);
   cudaMemsetAsync(ctx->f[1], 0, L.f1 - L.f0, ctx->stream);
@@ -219,6 +223,7 @@ int lbm_set_params(lbm_ctx *ctx, const lbm_params *p) {
   int rc = validate(ctx, p);
   if (rc != LBM_OK) return rc;
   drop_step_graphs(ctx);  // the kernels take the parameters by value
+  ctx->mom_valid = 0;     // the stored moments depend on the shift and the EOS
   ctx->params = *p;
   KParams &k = ctx->kp;
   k.RT = (float)(p->R * p->T);
@@ -286,6 +291,7 @@ int lbm_set_state(lbm_ctx *ctx, const float *rho0, const float *u0) {
   cudaGetLastError();
   cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
   launch_init(ctx, rho0, u0);
+  ctx->mom_valid = 0;
   int rc = check_cuda(ctx, "lbm_set_state");
   if (rc == LBM_OK) ctx->have_state = 1;
   return rc;
@@ -354,7 +360,11 @@ int lbm_step(lbm_ctx *ctx, int n) {
   // whole groups of GRAPH_STEPS steps replay a captured graph (one launch
   // instead of three to five per step); per-kernel profiling needs the
   // individual launches
-  while (n >= GRAPH_STEPS && !ctx->prof_on) {
+  // a captured group starts from valid moments when its steps produce them
+  if (n >= GRAPH_STEPS && !ctx->prof_on && !ctx->kp.inject_wait && !ctx->mom_valid &&
+      step_produces_moments(ctx))
+    launch_moments_current(ctx);
+  while (n >= GRAPH_STEPS && !ctx->prof_on && !ctx->kp.inject_wait) {
     cudaGraphExec_t g = step_graph(ctx);
     if (!g || cudaGraphLaunch(g, ctx->stream) != cudaSuccess) {
       cudaGetLastError();
@@ -365,6 +375,22 @@ int lbm_step(lbm_ctx *ctx, int n) {
   }
   for (int i = 0; i < n; ++i) launch_step(ctx);
   return check_cuda(ctx, "lbm_step");
+}
+
+int lbm_set_fused_moments(lbm_ctx *ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return LBM_ERR_ARG;
+  if (on != ctx->fuse_mom) {
+    drop_step_graphs(ctx);  // the captured steps take one path or the other
+    ctx->fuse_mom = on;
+    ctx->mom_valid = 0;
+  }
+  return LBM_OK;
+}
+
+int lbm_inject_wait_timeout(lbm_ctx *ctx) {
+  if (!ctx) return LBM_ERR_ARG;
+  ctx->kp.inject_wait = 1;
+  return LBM_OK;
 }
 
 int lbm_sync_status(lbm_ctx *ctx) {
@@ -428,6 +454,7 @@ int lbm_set_raw_state(lbm_ctx *ctx, const void *f) {
     cudaMemcpyAsync(ctx->fld.sb, (const char *)f + pops, 2 * (size_t)ctx->N * sizeof(float),
                     cudaMemcpyDeviceToDevice, ctx->stream);
   cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+  ctx->mom_valid = 0;
   int rc = check_cuda(ctx, "lbm_set_raw_state");
   if (rc == LBM_OK) ctx->have_state = 1;
   return rc;
@@ -447,6 +474,7 @@ int lbm_set_populations(lbm_ctx *ctx, const float *f) {
   cudaGetLastError();
   launch_set_populations(ctx, f);
   cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+  ctx->mom_valid = 0;
   int rc = check_cuda(ctx, "lbm_set_populations");
   if (rc == LBM_OK) ctx->have_state = 1;
   return rc;
@@ -514,6 +542,7 @@ void enqueue_segment(lbm_ctx *ctx, int n, char *pool, float *lam, float *lam_tmp
   // reads them from slot i-1 and writes them into slot i
   float *const own_sb = ctx->fld.sb;
   auto bases = [&](int i) { return (float *)(slot(i) + L.pops); };
+  ctx->mom_valid = 0;  // slot 0 holds the checkpoint just copied in
   // recompute: step i reads slot i-1, writes slot i and captures the fields
   // of state i-1 into slot i-1
   for (int i = 1; i < n; ++i) {
@@ -548,6 +577,7 @@ void enqueue_segment(lbm_ctx *ctx, int n, char *pool, float *lam, float *lam_tmp
   }
   launch_adjoint_partials_reduce(ctx, grad);
   if (lin != lam) cudaMemcpyAsync(lam, lin, 27 * (size_t)ctx->N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  ctx->mom_valid = 0;
 }
 
 // The segment sweep as a CUDA graph, captured once per (length, buffers) on
@@ -577,6 +607,7 @@ cudaGraphExec_t segment_graph(lbm_ctx *ctx, int n, char *pool, float *lam, float
   ctx->f[0] = own0;
   ctx->f[1] = own1;
   ctx->cur = own_cur;
+  view_moments(ctx);
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   const bool ok = cudaStreamEndCapture(ctx->capture_stream, &graph) == cudaSuccess && graph &&
@@ -624,6 +655,8 @@ int lbm_adjoint_segment(lbm_ctx *ctx, const void *ckpt, int n, void *state_pool,
   ctx->f[0] = own0;
   ctx->f[1] = own1;
   ctx->cur = own_cur;
+  view_moments(ctx);
+  ctx->mom_valid = 0;
   cudaMemcpyAsync(ctx->f[ctx->cur], ckpt, L.pops, cudaMemcpyDeviceToDevice, s);
   if (L.rest) cudaMemcpyAsync(ctx->fld.sb, (const char *)ckpt + L.pops, L.sbb, cudaMemcpyDeviceToDevice, s);
   ctx->have_state = 1;
@@ -658,6 +691,18 @@ void lbm_destroy(lbm_ctx *ctx) {
 }
 
 long long lbm_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int lbm_stored_moments(lbm_ctx *ctx, float *rho, float *j, float *mu0) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->have_state || !ctx->mom_valid) return fail(ctx, LBM_ERR_STATE, "no stored moments of the current state");
+  const size_t N = ctx->N;
+  const lbm::Moments &m = ctx->mom[ctx->cur];
+  cudaGetLastError();
+  if (rho) cudaMemcpyAsync(rho, m.rho, N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (j) cudaMemcpyAsync(j, m.j, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (mu0) cudaMemcpyAsync(mu0, m.mu0, N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream);
+  return check_cuda(ctx, "lbm_stored_moments");
+}
 
 int lbm_profile_enable(lbm_ctx *ctx, int on) {
   if (!ctx) return LBM_ERR_ARG;

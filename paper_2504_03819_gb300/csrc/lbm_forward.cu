@@ -2,7 +2,6 @@
 // over structure-of-arrays fields, plus initialisation, boundary marking,
 // population import/export and the FP64 diagnostics:
 //
-//   moments   rho, j from the populations (Eq. 11) + status check
 //   wet_rho   solid-node density from the wetting scheme (Eqs. 37-38)
 //   mu        mu = mu0(rho) - kappa lap rho on fluid nodes (Eqs. 2, 32)
 //   wet_mu    solid-node chemical potential (Eq. 36)
@@ -26,42 +25,6 @@ namespace {
 constexpr int BLOCK = 256;
 
 inline int blocks_for(long long n) { return (int)((n + BLOCK - 1) / BLOCK); }
-
-// ---------------------------------------------------------------------------
-// moments (Eq. 11) with the non-finite / EOS-domain check
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(BLOCK) k_moments(const T *__restrict__ f, const uint8_t *__restrict__ mask,
-                                                   const float *__restrict__ sb, float *__restrict__ rho,
-                                                   float *__restrict__ j, int *__restrict__ status, KParams kp) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  bool bad_nf = false, bad_dom = false;
-  if (n < kp.N && !(mask && mask[n])) {
-    const size_t N = (size_t)kp.N;
-    float s = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      float v = load_pop<T>(f + q * N + n);
-      s += v;
-      if (cx_of(q)) sx += cx_of(q) * v;
-      if (cy_of(q)) sy += cy_of(q) * v;
-      if (cz_of(q)) sz += cz_of(q) * v;
-    }
-    // the shifts carry mass rho_0 (or rho_b: sum_i E_i = 0) and no momentum
-    float r = s + (kp.shift_mode == LBM_SHIFT_REST ? sb[n] : kp.rho_shift);
-    rho[n] = r;
-    j[n] = sx;
-    j[N + n] = sy;
-    j[2 * N + n] = sz;
-    bad_nf = !(isfinite(r) && isfinite(sx) && isfinite(sy) && isfinite(sz));
-    bad_dom = !bad_nf && !(r > 0.0f && kp.b * r < 1.0f);
-  }
-  unsigned nf = __ballot_sync(0xffffffffu, bad_nf), dm = __ballot_sync(0xffffffffu, bad_dom);
-  if ((threadIdx.x & 31) == 0) {
-    if (nf) atomicOr(status, STATUS_NONFINITE);
-    if (dm) atomicOr(status, STATUS_DOMAIN);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // wetting boundary (Eqs. 36-38) on the listed solid nodes
@@ -432,15 +395,12 @@ __global__ void __launch_bounds__(RED_BLOCKS) k_reduce_final(const double *__res
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-template <typename T>
 void fields_impl(lbm_ctx *ctx, bool with_u) {
   const KParams &kp = ctx->kp;
   const Fields &d = ctx->fld;
-  const T *fin = (const T *)ctx->f[ctx->cur];
   const int g = blocks_for(kp.N);
   cudaStream_t s = ctx->stream;
-  k_moments<T><<<g, BLOCK, 0, s>>>(fin, ctx->mask, d.sb, d.rho, d.j, ctx->status, kp);
-  ctx->launches++;
+  launch_moments_current(ctx);  // the step's own moments pass: the same bits
   if (ctx->n_bnd) { k_wet_rho<<<blocks_for(ctx->n_bnd), BLOCK, 0, s>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, d.rho, kp); ctx->launches++; }
   k_mu<<<g, BLOCK, 0, s>>>(d.rho, ctx->mask, d.mu, kp);
   ctx->launches++;
@@ -490,12 +450,7 @@ void launch_wet_mu(lbm_ctx *ctx) {
   k_wet_mu<<<blocks_for(ctx->n_bnd), BLOCK, 0, ctx->stream>>>(ctx->bnd, ctx->n_bnd, ctx->nbr, ctx->fld.mu, ctx->kp);
 }
 
-void launch_fields(lbm_ctx *ctx, bool with_u) {
-  if (ctx->storage == LBM_F16)
-    fields_impl<__half>(ctx, with_u);
-  else
-    fields_impl<float>(ctx, with_u);
-}
+void launch_fields(lbm_ctx *ctx, bool with_u) { fields_impl(ctx, with_u); }
 
 void launch_init(lbm_ctx *ctx, const float *rho0, const float *u0) {
   const KParams &kp = ctx->kp;
@@ -550,7 +505,7 @@ void launch_set_populations(lbm_ctx *ctx, const float *in) {
 }
 
 const char *kernel_name(int id) {
-  static const char *names[K_COUNT] = {"moments", "wet_rho", "mu", "wet_mu", "uphi", "q", "collide"};
+  static const char *names[K_COUNT] = {"moments", "wet_rho", "mu", "wet_mu", "uphi", "q", "collide", "moments_edge"};
   return (id >= 0 && id < K_COUNT) ? names[id] : nullptr;
 }
 

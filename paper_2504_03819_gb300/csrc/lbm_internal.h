@@ -38,6 +38,7 @@ struct KParams {
   float ref_rho[2], ref_omb[2], ref_dmu[2];  // [0] vapour, [1] liquid: rho_r, 1 - b rho_r, mu0(rho_r) - mu_ref
   float ref_inv[2], ref_bomb[2];             // 1 / rho_r, b / (1 - b rho_r)
   float ref_bomb2[2];                        // b / (1 - b rho_r)^2
+  int inject_wait;  // failure-path test: block 0's first bounded wait waits on a barrier nothing completes
 };
 
 // Device views carved out of the caller's workspace.
@@ -54,6 +55,14 @@ struct Fields {
                //       moments kernel to the chemical-potential kernel
 };
 
+// Moments of a population state: rho, j and mu0(rho) - mu_ref of the fluid
+// nodes.  Two sets, one per population buffer (set k belongs to the state in
+// f[k]); the fused step writes the moments of the state it produces into the
+// other set, and Fields.rho / .j / .mu0 view the set of the current state.
+struct Moments {
+  float *rho, *j, *mu0;
+};
+
 // Adjoint scratch (reused between the stages of one adjoint step).
 struct AdjFields {
   float *u, *F, *Q, *phi;  // 3N each
@@ -68,6 +77,7 @@ enum KernelId {
   K_UPHI,
   K_Q,
   K_COLLIDE,
+  K_MOM_EDGE,
   K_COUNT
 };
 
@@ -115,6 +125,12 @@ struct lbm_ctx {
   float *sb_out;        // when set, the fused step writes the new shift bases here instead of over fld.sb
   const float *wall_u;  // caller's 3 N wall velocities (read at solid nodes), or null: walls at rest
   lbm::Fields fld;
+  lbm::Moments mom[2];  // moments of the state in f[0] / f[1] (fld views mom[cur])
+  int mom_valid;        // mom[cur] holds the moments of f[cur]
+  int no_mom;           // the step never produces the next moments itself (lbm_step_noalloc)
+  int fuse_mom;         // opt-in (lbm_set_fused_moments): the fused kernel produces the next moments
+  int mom_cfg;          // cluster launch of the fused step: 0 not chosen yet, 1 chosen, -1 unavailable
+  int mom_cx, mom_cy, mom_tz;  // its cluster shape (blocks) and planes per block
   double *red_partial;  // RED_BLOCKS * 2
   lbm::AdjFields adj;   // adjoint scratch
   double *adj_partial;  // per-block FP64 parameter-gradient partials
@@ -184,6 +200,15 @@ void launch_adjoint_init(lbm_ctx *ctx, const float *u0, const float *lam0, doubl
 void launch_objective(lbm_ctx *ctx, int kind, int wall_z, double *J, float *lam, double *grad);
 void launch_set_populations(lbm_ctx *ctx, const float *in);
 void drop_step_graphs(lbm_ctx *ctx);  // after a change the captured step graphs would miss (lbm_api.cu)
+void launch_moments_current(lbm_ctx *ctx);  // moments of f[cur] into mom[cur] (lbm_step_fused.cu)
+bool step_produces_moments(lbm_ctx *ctx);    // a step from f[cur] writes the moments of its output
+
+// Points the field views at the moment set of the current state.
+inline void view_moments(lbm_ctx *ctx) {
+  ctx->fld.rho = ctx->mom[ctx->cur].rho;
+  ctx->fld.j = ctx->mom[ctx->cur].j;
+  ctx->fld.mu0 = ctx->mom[ctx->cur].mu0;
+}
 const char *kernel_name(int id);
 
 // Counts a kernel launch of the context and, when per-kernel profiling is on,

@@ -84,6 +84,30 @@ template <> __device__ __forceinline__ void store_pop<__half>(__half *p, float v
   *p = __float2half_rn(v);
 }
 
+// ---- moments of one node (Eq. 11) ----------------------------------------
+// Sums of a node's 27 stored populations v[q]: s = sum_q v_q and the
+// momentum sums per axis as (+1 class) - (-1 class), grouped to keep FP32
+// rounding small.  Every kernel that forms moments (the moments passes, the
+// fused step's read-back of the state it wrote, the edge pass) uses this one
+// order, so the moments of a state are the same bits whichever path made
+// them.
+__device__ __forceinline__ void node_sums(const float (&v)[27], float &s, float &sx, float &sy, float &sz) {
+  s = 0.0f;
+  sx = 0.0f;
+  sy = 0.0f;
+  sz = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) s += v[q];
+#pragma unroll
+  for (int q = 0; q < 27; q += 3) sx += v[q + 2] - v[q];
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sy += v[a + 6 + 9 * g] - v[a + 9 * g];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) sz += v[p + 18] - v[p];
+}
+
 // ---- central-moment transform (Eq. 19) ----------------------------------
 // One axis: values (a, b, c) of the velocities -1, 0, +1 become the central
 // moments of order 0, 1, 2 about u.  With s = a + c, d = c - a:

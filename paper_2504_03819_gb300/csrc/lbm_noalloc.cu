@@ -26,7 +26,9 @@ constexpr size_t kScratchBytes = kStatusOff + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Host code cannot use g_noalloc_scratch as a device address: its device
-// address is looked up once per device with cudaGetSymbolAddress.
+// address is looked up once per device with cudaGetSymbolAddress.  The cached
+// address belongs to the device's primary context; it does not survive
+// cudaDeviceReset (or any other teardown of that context) in this process.
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_ptr[kMaxDevices];
@@ -81,6 +83,9 @@ extern "C" int lbm_step_noalloc(const float *f_in, float *f_out, const uint8_t *
   ctx.fld.Q = fl + 14 * n;
   ctx.fld.sb = fl + 17 * n;
   ctx.fld.mu0 = fl + 19 * n;
+  // one step: the moments of its output are not produced (one moment set)
+  ctx.mom[0] = ctx.mom[1] = lbm::Moments{ctx.fld.rho, ctx.fld.j, ctx.fld.mu0};
+  ctx.no_mom = 1;
   ctx.bnd = (int *)((char *)base + kBndOff);
   ctx.nbr = (uint32_t *)((char *)base + kNbrOff);
   ctx.inv_den = (float *)((char *)base + kInvDenOff);
@@ -116,5 +121,17 @@ extern "C" int lbm_step_noalloc(const float *f_in, float *f_out, const uint8_t *
   }
   ctx.have_state = 1;
   lbm::launch_step(&ctx);
-  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+  // the step's status word lives in the shared array: read it before the
+  // next call can clear it (a copy into a host int, no allocation)
+  int st = 0;
+  if (cudaMemcpyAsync(&st, ctx.status, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  if (st & lbm::STATUS_NONFINITE) return LBM_ERR_NONFINITE;
+  if (st & lbm::STATUS_DOMAIN) return LBM_ERR_DOMAIN;
+  if (st & lbm::STATUS_TIMEOUT) return LBM_ERR_TIMEOUT;
+  return LBM_OK;
 }

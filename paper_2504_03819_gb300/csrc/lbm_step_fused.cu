@@ -43,18 +43,8 @@ __global__ void __launch_bounds__(256) k_moments_v(const T *__restrict__ f, cons
     float v[27];
 #pragma unroll
     for (int q = 0; q < 27; ++q) v[q] = load_pop<T>(f + q * N + n);
-    // sums over the velocity components, grouped to keep FP32 rounding small
-    float s = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 27; ++q) s += v[q];
-#pragma unroll
-    for (int q = 0; q < 27; q += 3) sx += v[q + 2] - v[q];
-#pragma unroll
-    for (int g = 0; g < 3; ++g)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) sy += v[a + 6 + 9 * g] - v[a + 9 * g];
-#pragma unroll
-    for (int p = 0; p < 9; ++p) sz += v[p + 18] - v[p];
+    float s, sx, sy, sz;
+    node_sums(v, s, sx, sy, sz);
     const float r = s + (kp.shift_mode == LBM_SHIFT_REST ? sb[n] : kp.rho_shift);
     rho[n] = r;
     j[n] = sx;
@@ -92,17 +82,8 @@ __global__ void __launch_bounds__(256) k_moments_h2(const __half *__restrict__ f
     }
     auto finish = [&](const float (&v)[27], int n) {
       if (mask && mask[n]) return;
-      float s = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
-#pragma unroll
-      for (int q = 0; q < 27; ++q) s += v[q];
-#pragma unroll
-      for (int q = 0; q < 27; q += 3) sx += v[q + 2] - v[q];
-#pragma unroll
-      for (int g = 0; g < 3; ++g)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) sy += v[a + 6 + 9 * g] - v[a + 9 * g];
-#pragma unroll
-      for (int p = 0; p < 9; ++p) sz += v[p + 18] - v[p];
+      float s, sx, sy, sz;
+      node_sums(v, s, sx, sy, sz);
       const float r = s + (kp.shift_mode == LBM_SHIFT_REST ? sb[n] : kp.rho_shift);
       rho[n] = r;
       j[n] = sx;
@@ -259,6 +240,7 @@ struct FusedSmem {
   float uF[2][6][NT];     // u, F of the tile for planes z, z+1
   uint8_t solid[4][H1P];  // mask planes
   alignas(8) uint64_t bar;  // completion barrier of the population tile copy
+  uint64_t never;           // barrier no thread arrives at (failure-path test)
 };
 // the population tile of one plane, [q][y][x], staged by a tensor copy
 // behind FusedSmem at a 128-byte boundary
@@ -271,6 +253,25 @@ __device__ __forceinline__ int r5(int z) { return (z + 10) % 5; }  // z >= -2
 __device__ __forceinline__ int r4(int z) { return (z + 8) & 3; }
 __device__ __forceinline__ int r3(int z) { return (z + 6) % 3; }
 __device__ __forceinline__ int r2(int z) { return (z + 4) & 1; }
+
+// Split barrier of a thread-block cluster: arrive (release at cluster scope)
+// and wait (acquire at cluster scope), each executed by every thread of
+// every block of the cluster, alternately.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait;" ::: "memory"); }
+
+// population load through L2 only (values other blocks of the cluster wrote)
+template <typename T> __device__ __forceinline__ float load_cg(const T *p);
+template <> __device__ __forceinline__ float load_cg<float>(const float *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float load_cg<__half>(const __half *p) { return __half2float(__ldcg(p)); }
+
+// Where the fused step writes the moments of the state it produces (rho,
+// j, mu0 of the other moment set); rho == nullptr: it does not.
+struct MomArgs {
+  float *rho, *j, *mu0;
+  int crows;  // rows of one cluster of blocks (cluster height x TY); >= ny: it spans y
+  int zspan;  // one block's z range is the whole domain
+};
 
 template <typename T> __device__ __forceinline__ float to_f32(T v);
 template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
             const float *sb, float *sb_out, int *__restrict__ status, float *__restrict__ cap,
-            const float *__restrict__ wall_u, KParams kp, int TZ,
+            const float *__restrict__ wall_u, MomArgs mo, KParams kp, int TZ,
             const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
@@ -308,11 +309,15 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   const size_t N = (size_t)kp.N;
   constexpr bool rest = REST;
 
+  // failure-path test: block 0 makes its first wait on a barrier that no
+  // thread arrives at, so that bounded wait runs out
+  const bool inject = TMA && kp.inject_wait && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
   if (TMA) {
     // the first plane's copy is in flight while the field planes load
     if (tid == 0) {
       tma_prefetch_map(&tmap);
       mbar_init(&S.bar, 1);
+      if (inject) mbar_init(&S.never, 1);
       mbar_fence_init();
       mbar_arrive_expect_tx(&S.bar, FBYTES);
       tma_load_4d(smem_raw + FBUF_OFFSET, &tmap, &S.bar, x0, y0, z0, 0);
@@ -490,56 +495,10 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     i3a = i3b;
     i3b = t;
   };
-  for (int z = z0; z < z1; ++z, advance()) {
-    // publish mu'(z+2), rho/j(z+1); prefetch mu'(z+3), rho/j(z+2)
-    store(i5c, z + 1);
-    if (z + 1 < z1) fetch(z + 3, z + 2);
-    // populations of this node
-    const int n = x + nx * y + nxy * z;
-    const bool active = inside && (!MASK || !S.solid[r4(z)][c1]);
-    float f[27];
-    float rb = kp.rho_shift, cb = 0.0f;
-    if (rest && active) {
-      rb = sb[n];
-      cb = sb[N + n];
-    }
-    if (TMA) {
-      const bool ok = mbar_wait_bounded(&S.bar, (uint32_t)(z - z0) & 1u);
-      if (active) {
-#pragma unroll
-        for (int q = 0; q < 27; ++q) f[q] = to_f32<T>(fbuf[q * NT + tid]);
-      }
-      // every thread has its populations: the buffer takes the next plane
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-          atomicOr(status, STATUS_TIMEOUT);
-          mbar_wait_bounded(&S.bar, (uint32_t)(z - z0) & 1u);  // let the late copy land before exit
-        }
-        return;
-      }
-      if (tid == 0 && z + 1 < z1) {
-        mbar_arrive_expect_tx(&S.bar, FBYTES);
-        tma_load_4d(smem_raw + FBUF_OFFSET, &tmap, &S.bar, x0, y0, z + 1, 0);
-      }
-    } else {
-      if (active) {
-#pragma unroll
-        for (int q = 0; q < 27; ++q) f[q] = load_pop<T>(fin + q * N + n);
-      }
-      __syncthreads();
-    }
-    fields(z + 1, true, i5a, i5b, i5c, i3b);
-    __syncthreads();
-    if (!active) {
-      if (cap && inside) {  // solid node: its wetting rho and mu', no flow
-        cap[n] = S.rho[r4(z)][c1];
-        cap[N + n] = S.mu[i5a][(ty + 2) * H2X + tx + 2];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) cap[(2 + c) * N + n] = 0.0f;
-      }
-      continue;
-    }
 
+  // corrections, collision and push of fluid node n of plane z (its
+  // populations in f, the shift basis of its stored state in rb, cb)
+  auto update = [&](int z, int n, float (&f)[27], float rb, float cb) {
     // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa phi_a(x + c_q), partial sums
     // per plane
     const float *p0 = S.phi[i3m][0], *p1 = S.phi[i3a][0], *p2 = S.phi[i3b][0];
@@ -626,6 +585,124 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       sb_out[n] = r_own;
       sb_out[N + n] = c_own;
     }
+  };
+
+  // Moments of the output state (Eq. 11), when mo.rho is set: once every
+  // block of the cluster has pushed planes up to d + 1, plane d of fout holds
+  // all of its populations at the nodes whose 27 sources lie in the
+  // cluster's columns and this block's z range, and this thread sums its
+  // node there (from L2: the planes were just written).  The first and last
+  // rows of the cluster (unless it spans y) and the first and last plane of
+  // the z range (unless it spans z) take populations from other clusters or
+  // blocks: the edge pass completes them after the kernel.
+  const bool mom = mo.rho != nullptr;
+  bool yedge = false;
+  if (mom && mo.crows < ny) {
+    const int lo = (y0 / mo.crows) * mo.crows, hi = min(lo + mo.crows, ny) - 1;
+    yedge = y == lo || y == hi;
+  }
+  auto readback = [&](int d) {
+    bool nf = false, dm = false;
+    const int nd = x + nx * y + nxy * d;
+    if (inside && !yedge && !(MASK && mask[nd])) {
+      float v[27];
+#pragma unroll
+      for (int q = 0; q < 27; ++q) v[q] = load_cg<T>(fout + q * N + nd);
+      float sr, sx, sy, sz;
+      node_sums(v, sr, sx, sy, sz);
+      const float r = sr + (rest ? sb_out[nd] : kp.rho_shift);
+      mo.rho[nd] = r;
+      mo.j[nd] = sx;
+      mo.j[N + nd] = sy;
+      mo.j[2 * N + nd] = sz;
+      mo.mu0[nd] = mu0_vdw(r, kp);
+      nf = !(isfinite(r) && isfinite(sx) && isfinite(sy) && isfinite(sz));
+      dm = !nf && !(r > 0.0f && kp.b * r < 1.0f);
+    }
+    const unsigned bn = __ballot_sync(0xffffffffu, nf), bd = __ballot_sync(0xffffffffu, dm);
+    if ((tid & 31) == 0) {
+      if (bn) atomicOr(status, STATUS_NONFINITE);
+      if (bd) atomicOr(status, STATUS_DOMAIN);
+    }
+  };
+
+  // A block whose bounded wait gave up stops its work; in a cluster launch it
+  // keeps taking part in the cluster barriers so that no other block waits
+  // for it forever.
+  bool dead = false;
+  if (mom) cluster_arrive();
+  for (int z = z0; z < z1; ++z, advance()) {
+    if (!dead) {
+      // publish mu'(z+2), rho/j(z+1); prefetch mu'(z+3), rho/j(z+2)
+      store(i5c, z + 1);
+      if (z + 1 < z1) fetch(z + 3, z + 2);
+      // populations of this node
+      const int n = x + nx * y + nxy * z;
+      const bool active = inside && (!MASK || !S.solid[r4(z)][c1]);
+      float f[27];
+      float rb = kp.rho_shift, cb = 0.0f;
+      if (rest && active) {
+        rb = sb[n];
+        cb = sb[N + n];
+      }
+      if (TMA) {
+        const bool ok = (inject && z == z0) ? mbar_wait_bounded(&S.never, 0u, INJECTED_WAIT_NS)
+                                            : mbar_wait_bounded(&S.bar, (uint32_t)(z - z0) & 1u);
+        if (active) {
+#pragma unroll
+          for (int q = 0; q < 27; ++q) f[q] = to_f32<T>(fbuf[q * NT + tid]);
+        }
+        // every thread has its populations: the buffer takes the next plane
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+            mbar_wait_bounded(&S.bar, (uint32_t)(z - z0) & 1u);  // let the late copy land before exit
+          }
+          if (!mom) return;
+          dead = true;
+        } else if (tid == 0 && z + 1 < z1) {
+          // the block's reads of this plane's tile (ordered before this point
+          // by the barrier) complete before the copy of the next plane lands
+          // in the same buffer
+          fence_proxy_async_smem();
+          mbar_arrive_expect_tx(&S.bar, FBYTES);
+          tma_load_4d(smem_raw + FBUF_OFFSET, &tmap, &S.bar, x0, y0, z + 1, 0);
+        }
+      } else {
+        if (active) {
+#pragma unroll
+          for (int q = 0; q < 27; ++q) f[q] = load_pop<T>(fin + q * N + n);
+        }
+        __syncthreads();
+      }
+      if (!dead) {
+        fields(z + 1, true, i5a, i5b, i5c, i3b);
+        __syncthreads();
+        if (active) {
+          update(z, n, f, rb, cb);
+        } else if (cap && inside) {  // solid node: its wetting rho and mu', no flow
+          cap[n] = S.rho[r4(z)][c1];
+          cap[N + n] = S.mu[i5a][(ty + 2) * H2X + tx + 2];
+#pragma unroll
+          for (int c = 0; c < 9; ++c) cap[(2 + c) * N + n] = 0.0f;
+        }
+      }
+    }
+    if (mom) {
+      cluster_wait();  // every block of the cluster has pushed plane z - 1
+      if (!dead && z - 2 >= z0 + 1) readback(z - 2);
+      cluster_arrive();
+    }
+  }
+  if (mom) {
+    cluster_wait();  // ... and every plane of its z range
+    if (!dead) {
+      if (z1 - 2 >= z0 + 1) readback(z1 - 2);
+      if (mo.zspan) {  // the z range wraps onto itself: its end planes are complete too
+        readback(z1 - 1);
+        readback(z0);
+      }
+    }
   }
 }
 
@@ -658,6 +735,8 @@ template <auto K> void ensure_smem(size_t bytes) {
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(done.load() & bit)) {
     cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(K, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);  // clusters of up to 16 blocks
+    cudaGetLastError();
     done.fetch_or(bit);
   }
 }
@@ -749,19 +828,152 @@ const CUtensorMap *population_tmap(lbm_ctx *ctx, const void *p) {
   return e.ok ? &e.map : nullptr;
 }
 
+// Moments of the output state at the nodes the fused step's read-back
+// leaves out (Eq. 11), summed like every other moments kernel: mode 0 takes
+// the first and last row of each cluster of blocks (crows rows) in every
+// plane, mode 1 the other rows of the first and last plane of each block's
+// z range (tz planes).  Grids: (ceil(nx / 256), 2 ceil(ny / crows), nz) and
+// (ceil(nx / 256), ny, 2 ceil(nz / tz)).
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments_edge(const T *__restrict__ f, const uint8_t *__restrict__ mask,
+                                                      const float *__restrict__ sb, float *__restrict__ rho,
+                                                      float *__restrict__ j, float *__restrict__ mu0,
+                                                      int *__restrict__ status, KParams kp, int crows, int tz,
+                                                      int mode) {
+  const int x = blockIdx.x * 256 + threadIdx.x;
+  int y, z;
+  if (mode == 0) {
+    const int e = blockIdx.y, lo = (e >> 1) * crows, hi = min(lo + crows, kp.ny) - 1;
+    if ((e & 1) && hi == lo) return;  // a one-row cluster has one edge row (whole block)
+    y = (e & 1) ? hi : lo;
+    z = blockIdx.z;
+  } else {
+    const int e = blockIdx.z, lo = (e >> 1) * tz, hi = min(lo + tz, kp.nz) - 1;
+    if ((e & 1) && hi == lo) return;
+    z = (e & 1) ? hi : lo;
+    y = blockIdx.y;
+    if (crows < kp.ny) {  // edge rows are mode 0's
+      const int ylo = (y / crows) * crows, yhi = min(ylo + crows, kp.ny) - 1;
+      if (y == ylo || y == yhi) return;
+    }
+  }
+  bool bad_nf = false, bad_dom = false;
+  const int n = x + kp.nx * (y + kp.ny * z);
+  if (x < kp.nx && !(mask && mask[n])) {
+    const size_t N = (size_t)kp.N;
+    float v[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) v[q] = load_pop<T>(f + q * N + n);
+    float s, sx, sy, sz;
+    node_sums(v, s, sx, sy, sz);
+    const float r = s + (kp.shift_mode == LBM_SHIFT_REST ? sb[n] : kp.rho_shift);
+    rho[n] = r;
+    j[n] = sx;
+    j[N + n] = sy;
+    j[2 * N + n] = sz;
+    mu0[n] = mu0_vdw(r, kp);
+    bad_nf = !(isfinite(r) && isfinite(sx) && isfinite(sy) && isfinite(sz));
+    bad_dom = !bad_nf && !(r > 0.0f && kp.b * r < 1.0f);
+  }
+  const unsigned nf = __ballot_sync(0xffffffffu, bad_nf), dm = __ballot_sync(0xffffffffu, bad_dom);
+  if ((threadIdx.x & 31) == 0) {
+    if (nf) atomicOr(status, STATUS_NONFINITE);
+    if (dm) atomicOr(status, STATUS_DOMAIN);
+  }
+}
+
+// Cluster launch of the fused step that also produces the next moments:
+// the cluster spans every block column in x (so no population crosses its x
+// edges) and as many block rows as fit in 16 blocks; z ranges of at least 4
+// planes.  Chosen once per context from the occupancy of the kernel K.
+template <auto K>
+bool mom_config(lbm_ctx *ctx, size_t smem) {
+  if (ctx->mom_cfg) return ctx->mom_cfg > 0;
+  ctx->mom_cfg = -1;
+  const KParams &kp = ctx->kp;
+  const int gx = (kp.nx + TX - 1) / TX, gy = (kp.ny + TY - 1) / TY;
+  if (ctx->no_mom || gx > 16 || kp.nz < 3) return false;
+  for (int cy = 16 / gx; cy >= 1; --cy) {
+    if (gy % cy) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(gx, gy, 1);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = gx;
+    at.val.clusterDim.y = cy;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, K, &cfg) != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    int tz = z_chunk(gx * gy, kp.nz, clusters * gx * cy, 2);
+    if (tz < kp.nz) tz = max(tz, 4);
+    if (tz >= kp.nz) tz = kp.nz;
+    ctx->mom_cx = gx;
+    ctx->mom_cy = cy;
+    ctx->mom_tz = tz;
+    ctx->mom_cfg = 1;
+    return true;
+  }
+  return false;
+}
+
+// Launches k_fused; with the tensor-copy path and a usable cluster shape it
+// also writes the moments of the output state into the other moment set
+// (returns true: the edge pass must follow).
+// The cluster shape from a representative instantiation: every k_fused
+// instantiation has the same launch bounds and shared memory, so the same
+// occupancy.
+template <typename T>
+bool mom_config_t(lbm_ctx *ctx) {
+  constexpr auto K = k_fused<T, false, true, false, true, true>;
+  constexpr size_t sm = fused_smem_size<T>(true);
+  ensure_smem<K>(sm);
+  return mom_config<K>(ctx, sm);
+}
+
 template <typename T, bool MASK, bool TMA, bool WALLV, bool UNIT, bool REST>
-void launch_fused_u(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
+bool launch_fused_u(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map, bool produce) {
   const KParams &kp = ctx->kp;
   const Fields &d = ctx->fld;
   constexpr size_t sm = fused_smem_size<T>(TMA);
   constexpr auto K = k_fused<T, MASK, TMA, WALLV, UNIT, REST>;
   ensure_smem<K>(sm);
-  const int xyb = ((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY);
-  const int tz = z_chunk(xyb, kp.nz, resident_slots<K>(NT, sm), 2);
-  const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, (kp.nz + tz - 1) / tz);
-  K<<<grid, NT, sm, ctx->stream>>>(fin, fout, MASK ? ctx->mask : nullptr, d.rho, d.j, d.mu, d.sb,
-                                   ctx->sb_out ? ctx->sb_out : d.sb, ctx->status,
-                                   ctx->capture, WALLV ? ctx->wall_u : nullptr, kp, tz, map);
+  const int gx = (kp.nx + TX - 1) / TX, gy = (kp.ny + TY - 1) / TY;
+  float *sb_out = ctx->sb_out ? ctx->sb_out : d.sb;
+  const uint8_t *mask = MASK ? ctx->mask : nullptr;
+  const float *wall_u = WALLV ? ctx->wall_u : nullptr;
+  if (TMA && produce) {
+    const Moments &m = ctx->mom[1 - ctx->cur];
+    MomArgs mo{m.rho, m.j, m.mu0, ctx->mom_cy * TY, ctx->mom_tz >= kp.nz ? 1 : 0};
+    const int tz = ctx->mom_tz;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(gx, gy, (kp.nz + tz - 1) / tz);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = ctx->mom_cx;
+    at.val.clusterDim.y = ctx->mom_cy;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, K, fin, fout, mask, (const float *)d.rho, (const float *)d.j, (const float *)d.mu,
+                       (const float *)d.sb, sb_out, ctx->status, ctx->capture, wall_u, mo, kp, tz, map);
+    return true;
+  }
+  const int tz = z_chunk(gx * gy, kp.nz, resident_slots<K>(NT, sm), 2);
+  const dim3 grid(gx, gy, (kp.nz + tz - 1) / tz);
+  const MomArgs none{nullptr, nullptr, nullptr, 0, 0};
+  K<<<grid, NT, sm, ctx->stream>>>(fin, fout, mask, d.rho, d.j, d.mu, d.sb, sb_out, ctx->status, ctx->capture,
+                                   wall_u, none, kp, tz, map);
+  return false;
 }
 
 // every rate but omega_1 equal to 1 (exactly: each 1 - omega_i is 0)
@@ -772,39 +984,51 @@ bool unit_rates(const KParams &kp) {
 }
 
 template <typename T, bool MASK, bool TMA, bool WALLV>
-void launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map) {
+bool launch_fused_k(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map, bool produce) {
   const bool unit = unit_rates(ctx->kp), rest = ctx->kp.shift_mode == LBM_SHIFT_REST;
-  if (unit && rest)
-    launch_fused_u<T, MASK, TMA, WALLV, true, true>(ctx, fin, fout, map);
-  else if (unit)
-    launch_fused_u<T, MASK, TMA, WALLV, true, false>(ctx, fin, fout, map);
-  else if (rest)
-    launch_fused_u<T, MASK, TMA, WALLV, false, true>(ctx, fin, fout, map);
-  else
-    launch_fused_u<T, MASK, TMA, WALLV, false, false>(ctx, fin, fout, map);
+  if (unit && rest) return launch_fused_u<T, MASK, TMA, WALLV, true, true>(ctx, fin, fout, map, produce);
+  if (unit) return launch_fused_u<T, MASK, TMA, WALLV, true, false>(ctx, fin, fout, map, produce);
+  if (rest) return launch_fused_u<T, MASK, TMA, WALLV, false, true>(ctx, fin, fout, map, produce);
+  return launch_fused_u<T, MASK, TMA, WALLV, false, false>(ctx, fin, fout, map, produce);
 }
 
 template <typename T>
-void launch_fused(lbm_ctx *ctx, const void *fin_v, void *fout_v) {
+bool launch_fused(lbm_ctx *ctx, const void *fin_v, void *fout_v, bool produce) {
   const T *fin = static_cast<const T *>(fin_v);
   T *fout = static_cast<T *>(fout_v);
   const CUtensorMap *map = population_tmap(ctx, fin_v);
   const bool moving = ctx->mask && ctx->wall_u;
   if (map) {
-    if (moving)
-      launch_fused_k<T, true, true, true>(ctx, fin, fout, *map);
-    else if (ctx->mask)
-      launch_fused_k<T, true, true, false>(ctx, fin, fout, *map);
-    else
-      launch_fused_k<T, false, true, false>(ctx, fin, fout, *map);
-  } else {
-    // rows that a tensor copy cannot describe: per-thread loads, the mask
-    // checks compiled in (an all-fluid domain has an all-zero solid plane)
-    static const CUtensorMap unused{};
-    if (moving)
-      launch_fused_k<T, true, false, true>(ctx, fin, fout, unused);
-    else
-      launch_fused_k<T, true, false, false>(ctx, fin, fout, unused);
+    if (moving) return launch_fused_k<T, true, true, true>(ctx, fin, fout, *map, produce);
+    if (ctx->mask) return launch_fused_k<T, true, true, false>(ctx, fin, fout, *map, produce);
+    return launch_fused_k<T, false, true, false>(ctx, fin, fout, *map, produce);
+  }
+  // rows that a tensor copy cannot describe: per-thread loads, the mask
+  // checks compiled in (an all-fluid domain has an all-zero solid plane)
+  static const CUtensorMap unused{};
+  if (moving) return launch_fused_k<T, true, false, true>(ctx, fin, fout, unused, false);
+  return launch_fused_k<T, true, false, false>(ctx, fin, fout, unused, false);
+}
+
+// the edge pass after a fused step that produced the next moments
+template <typename T>
+void launch_edge(lbm_ctx *ctx, const void *fout) {
+  const KParams &kp = ctx->kp;
+  const Moments &m = ctx->mom[1 - ctx->cur];
+  const float *sb = ctx->sb_out ? ctx->sb_out : ctx->fld.sb;
+  const int crows = ctx->mom_cy * TY, tz = ctx->mom_tz;
+  const int gx = (kp.nx + 255) / 256;
+  if (crows < kp.ny) {
+    const dim3 g(gx, 2 * ((kp.ny + crows - 1) / crows), kp.nz);
+    k_moments_edge<T><<<g, 256, 0, ctx->stream>>>((const T *)fout, ctx->mask, sb, m.rho, m.j, m.mu0, ctx->status,
+                                                  kp, crows, tz, 0);
+    ctx->launches++;
+  }
+  if (tz < kp.nz) {
+    const dim3 g(gx, kp.ny, 2 * ((kp.nz + tz - 1) / tz));
+    k_moments_edge<T><<<g, 256, 0, ctx->stream>>>((const T *)fout, ctx->mask, sb, m.rho, m.j, m.mu0, ctx->status,
+                                                  kp, crows, tz, 1);
+    ctx->launches++;
   }
 }
 
@@ -819,27 +1043,51 @@ void launch_moments_mu(lbm_ctx *ctx) {
   if (ctx->n_bnd) launch_wet_mu(ctx);
 }
 
-void launch_step_fused(lbm_ctx *ctx) {
-  const void *fin = ctx->f[ctx->cur];
-  void *fout = ctx->f[1 - ctx->cur];
+void launch_moments_current(lbm_ctx *ctx) {
   {
     TimedLaunch t(ctx, K_MOMENTS);
     launch_moments(ctx);
   }
+  ctx->mom_valid = 1;
+}
+
+// Whether a step from the current state also produces the next state's
+// moments: the tensor-copy instantiations with a usable cluster shape.
+bool step_produces_moments(lbm_ctx *ctx) {
+  if (!ctx->fuse_mom || ctx->no_mom || !population_tmap(ctx, ctx->f[ctx->cur])) return false;
+  return ctx->storage == LBM_F16 ? mom_config_t<__half>(ctx) : mom_config_t<float>(ctx);
+}
+
+void launch_step_fused(lbm_ctx *ctx) {
+  const void *fin = ctx->f[ctx->cur];
+  void *fout = ctx->f[1 - ctx->cur];
+  // the separate moments pass, unless the previous fused step produced them
+  const bool produce = step_produces_moments(ctx);
+  if (!produce || !ctx->mom_valid) launch_moments_current(ctx);
   if (ctx->n_bnd) launch_wet_rho(ctx);
   {
     TimedLaunch t(ctx, K_MU);
     launch_mu_z(ctx);
   }
   if (ctx->n_bnd) launch_wet_mu(ctx);
+  bool produced;
   {
     TimedLaunch t(ctx, K_COLLIDE);
-    if (ctx->storage == LBM_F16)
-      launch_fused<__half>(ctx, fin, fout);
-    else
-      launch_fused<float>(ctx, fin, fout);
+    produced = ctx->storage == LBM_F16 ? launch_fused<__half>(ctx, fin, fout, produce)
+                                       : launch_fused<float>(ctx, fin, fout, produce);
   }
+  if (produced) {
+    TimedLaunch t(ctx, K_MOM_EDGE);
+    ctx->launches--;  // launch_edge counts its launches (zero to two)
+    if (ctx->storage == LBM_F16)
+      launch_edge<__half>(ctx, fout);
+    else
+      launch_edge<float>(ctx, fout);
+  }
+  ctx->kp.inject_wait = 0;  // the injected wait is one-shot
   ctx->cur = 1 - ctx->cur;
+  view_moments(ctx);
+  ctx->mom_valid = produced ? 1 : 0;
 }
 
 }  // namespace lbm

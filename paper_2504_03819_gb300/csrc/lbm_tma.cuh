@@ -52,13 +52,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // waits for the phase with the given parity to complete; false after
-// TMA_WAIT_NS without completion
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// limit_ns nanoseconds without completion
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = TMA_WAIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > TMA_WAIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
+}
+
+// bound of the injected wait of the failure-path test (lbm_inject_wait_timeout)
+constexpr unsigned long long INJECTED_WAIT_NS = 1000000ull;
+
+// Orders this thread's (and, through a preceding barrier, the block's)
+// ordinary shared-memory accesses before its later tensor copies: a buffer
+// just read with ld.shared must not be overwritten by the next
+// cp.async.bulk.tensor (another memory proxy) until those reads are done.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // tiled 4-D tensor load of one box into shared memory; completion is

@@ -58,6 +58,18 @@ CASES = {
     # the same staging with walls and hydrophilic wetting (FP32 rows only)
     "wall_tiles": dict(n=(36, 10, 9), walls=(0, 8), radius=3.5, sessile=True, u=(0.01, 0.0, 0.0),
                        p=dict(wetting_mode=1, wetting_value=1.2)),
+    # general rates on the tensor-copy path (rows of 16-byte multiples in
+    # FP32 and FP16): two tiles in x with a ragged tail, three in y
+    "tiles_rates": dict(n=(40, 10, 9), walls=(), radius=3.5, u=(0.02, -0.01, 0.01),
+                        p=dict(omega=[1.0, 1.6, 1.2, 0.9, 1.1, 1.3, 0.8, 1.4, 1.05, 0.95, 1.5])),
+    # the same with populations stored minus the constant shift w_i rho_0
+    "tiles_rates_const": dict(n=(40, 10, 9), walls=(), radius=3.5, u=(0.02, -0.01, 0.01), const_shift=True,
+                              p=dict(omega=[1.0, 1.6, 1.2, 0.9, 1.1, 1.3, 0.8, 1.4, 1.05, 0.95, 1.5])),
+    # walls, hydrophobic (delta-rho) wetting and general rates on the
+    # tensor-copy path in FP32 and FP16 (40-wide rows)
+    "wall_tiles_delta": dict(n=(40, 8, 10), walls=(0, 9), radius=3.5, sessile=True, u=(0.01, 0.0, 0.0),
+                             p=dict(wetting_mode=2, wetting_value=0.7,
+                                    omega=[1.0, 1.3, 1.1, 0.95, 1.05, 1.2, 0.9, 1.1, 1.0, 0.9, 1.2])),
     # paper EOS, 0.7 T_c, kappa = 0.02, degenerate 1 x 1 x n flat interface
     "flat_paper_1d": dict(n=(1, 1, 48), walls=(), slab=24, u=(0.0, 0.0, 0.0),
                           p=dict(a=A392, t=0.7, kappa=0.02, nu=0.15)),
@@ -78,6 +90,9 @@ def build(name: str):
     else:
         rho0 = I.droplet(nx, ny, nz, c["radius"], p.rho_l, p.rho_v)
     u0 = I.uniform_velocity(nx, ny, nz, c["u"])
+    if c.get("const_shift"):
+        p.shift_mode = 0
+        p.rho_shift = 2 * p.rho_l * p.rho_v / (p.rho_l + p.rho_v)
     return dict(n=(nx, ny, nz), p=p, mask=mask, rho0=f32(rho0), u0=f32(u0))
 
 

@@ -154,6 +154,35 @@ def test_rollout_gradient_matches_fp64_adjoint(objective):
     assert relmax(g_rho0, ref["rho0"]) < 1e-3
 
 
+def test_wall_workload_copy_gradient_matches_fp64_adjoint():
+    """Scaled copy of the differentiable droplet-on-a-wall workload (64^3, R =
+    16, K = 100): 16^3 with solid planes z = 0 and 15, a hemisphere of R = 4
+    with N(0, 1e-3) noise from default_rng(12345) on the initial density,
+    phi-wetting 1.2 and all rates 1, at 0.85 T_c with the paper's EOS
+    coefficient and kappa (a = 9/392, kappa = 0.02: with a = 9/49, kappa =
+    0.01 this workload goes non-finite).  Contact-line radius after 40 steps
+    with checkpoints every 10 steps (four segments, each recomputed from its
+    checkpoint): dJ/d kappa, omega_1, phi and the initial density against the
+    oracle's FP64 reverse mode, to the gradient contract 1e-3."""
+    from _cases import A392, vdw, f32
+    n, T, K = 16, 40, 10
+    p = vdw(a=A392, t=0.85, kappa=0.02, wetting_mode=1, wetting_value=1.2)
+    mask = I.wall_mask(n, n, n, planes=(0, n - 1))
+    rho0 = f32(I.add_noise(I.sessile_droplet(n, n, n, 4.0, p.rho_l, p.rho_v), 1e-3, seed=12345))
+    d = Domain(n, n, n, "f32", solid_mask=mask)
+    d.set_params(p)
+    J, grad, g_rho0 = rollout_gradient(d, torch.from_numpy(rho0).float(), None, T, K, Bd.OBJ_CONTACT_RADIUS,
+                                       wall_z=0)
+    solid = torch.from_numpy(mask.astype(bool))
+    ref = OA.gradients(torch.from_numpy(rho0), None, solid, oracle_params(p), T, "contact_radius")
+    assert J == pytest.approx(ref["J"], rel=1e-5)
+    gg = grad.cpu()
+    assert float(gg[0]) == pytest.approx(ref["kappa"], rel=1e-3)
+    assert float(gg[2]) == pytest.approx(float(ref["omega"][1]), rel=1e-3)
+    assert float(gg[12]) == pytest.approx(ref["wetting_value"], rel=1e-3)
+    assert relmax(g_rho0, ref["rho0"]) < 1e-3
+
+
 def test_autograd_function_backward():
     p, mask, rho0 = sessile_case(mode=2, value=0.6)
     n = 8

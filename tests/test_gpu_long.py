@@ -82,3 +82,52 @@ def test_droplet_thousand_steps_through_tensor_copies(storage, rho_tol, u_tol):
     if u_tol is not None:
         assert absd(m["u"], ref["u"]) < u_tol
     assert m["mass"] == pytest.approx(float(ref["mass"]), rel=1e-6 if storage == "f32" else 1e-4)
+
+
+def _long_case(name: str):
+    """GPU inputs of a scaled workload copy, built from the same generator
+    calls as the script that wrote the oracle's result."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    from long_cases import EOS, LONG_CASES
+    c = LONG_CASES[name]
+    om = [1.0] * 11
+    om[1] = c["omega1"]
+    p = vdw(EOS["a"], EOS["t_over_tc"], EOS["kappa"], omega=om, wetting_mode=c["wetting_mode"],
+            wetting_value=c["wetting_value"])
+    nx, ny, nz = c["n"]
+    if c["walls"]:
+        rho0 = I.sessile_droplet(nx, ny, nz, c["radius"], p.rho_l, p.rho_v, wall_z=c["walls"][0] + 0.5,
+                                 width=c["width"])
+    else:
+        rho0 = I.droplet(nx, ny, nz, c["radius"], p.rho_l, p.rho_v, width=c["width"])
+    u0 = I.uniform_velocity(nx, ny, nz, c["u"])
+    mask = I.wall_mask(nx, ny, nz, planes=c["walls"])
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", f"long_{name}.npz"))
+    return c, p, rho0.astype(np.float32), u0.astype(np.float32), mask, ref
+
+
+@pytest.mark.parametrize("name", ["droplet24", "moving24", "wall32"])
+@pytest.mark.parametrize("storage,rho_tol,u_tol", [("f32", 1e-5, 1e-6), ("f16", 1e-3, None)])
+def test_workload_copies_thousand_steps(name, storage, rho_tol, u_tol):
+    """Scaled copies of the stationary droplet, the moving droplet (omega_1 =
+    1.6, U = (0.05, 0.02, 0)) and the droplet on a phi-wetting wall
+    (tests/golden/long_cases.py) after 1000 steps against the FP64 oracle's
+    fields written by tests/golden/make_long_parity.py: the method's
+    precision contract (FP32 storage: relative density 1e-5, |du| 1e-6; FP16
+    storage: relative density 1e-3) on the fluid nodes, and the fluid mass."""
+    c, p, rho0, u0, mask, ref = _long_case(name)
+    nx, ny, nz = c["n"]
+    d = Domain(nx, ny, nz, storage, solid_mask=mask if mask.any() else None)
+    d.set_params(p)
+    d.set_state(torch.from_numpy(rho0), torch.from_numpy(u0))
+    d.step(int(ref["steps"]))
+    assert d.sync_status() == 0
+    m = d.moments()
+    fl = torch.from_numpy(~mask.astype(bool))
+    r_ref = torch.from_numpy(ref["rho"].astype(np.float64))
+    assert rel(m["rho"][fl], r_ref[fl]) < rho_tol
+    if u_tol is not None:
+        assert absd(m["u"], torch.from_numpy(ref["u"].astype(np.float64))) < u_tol
+    assert m["mass"] == pytest.approx(float(ref["mass"]), rel=1e-6 if storage == "f32" else 1e-4)

@@ -157,7 +157,16 @@ def test_constant_shift_mode_fifty_steps(name):
     assert absd(m["u"], ref["u"]) < 1e-6
 
 
-@pytest.mark.parametrize("name", ["droplet_periodic", "droplet_tiles", "droplet_odd"])
+# FP16 storage: periodic droplets on both load paths, walls with phi- and
+# delta-rho wetting on the per-thread-load path (wall_phi: 11-wide rows,
+# wall_tiles: 36 halves = 72 bytes) and on the tensor-copy path
+# (wall_tiles_delta: 40 halves = 80 bytes, general rates), general rates
+# without walls (tiles_rates)
+FP16_CASES = ["droplet_periodic", "droplet_tiles", "droplet_odd", "wall_phi", "wall_tiles", "wall_tiles_delta",
+              "tiles_rates"]
+
+
+@pytest.mark.parametrize("name", FP16_CASES)
 def test_fp16_storage_fifty_steps(name):
     case = build(name)
     p = case["p"]
@@ -169,7 +178,31 @@ def test_fp16_storage_fifty_steps(name):
     solid = torch.from_numpy(case["mask"].astype(bool))
     op = oracle_params(p)
     ref = S.macroscopic(S.run(oracle_init(case), solid, op, 50), solid, op)
-    assert rel(m["rho"], ref["rho"]) < 1e-3
+    fl = fluid(case)
+    assert rel(m["rho"][fl], ref["rho"][fl]) < 1e-3
+    assert m["mass"] == pytest.approx(float(ref["mass"]), rel=1e-4)
+
+
+@pytest.mark.parametrize("name", ["wall_phi", "wall_tiles", "wall_tiles_delta"])
+def test_fp16_storage_one_step_with_walls(name):
+    """One FP16-storage step with bounce-back and wetting from a perturbed
+    state: the stored values carry FP16 rounding (2^-11 relative to the
+    shifted population), so density and velocity agree with the FP64 step
+    to about 1e-4; the bounds are the FP16 contract (1e-3 relative density)
+    and 1e-4 in |du|."""
+    case = build(name)
+    fr = perturbed(case, oracle_init(case), seed=23)
+    d = gpu(case, "f16")
+    d.set_populations(fr.float())
+    d.step(1)
+    assert d.sync_status() == 0
+    m = d.moments()
+    solid = torch.from_numpy(case["mask"].astype(bool))
+    op = oracle_params(case["p"])
+    ref = S.macroscopic(S.step(fr, solid, op), solid, op)
+    fl = fluid(case)
+    assert rel(m["rho"][fl], ref["rho"][fl]) < 1e-3
+    assert absd(m["u"], ref["u"]) < 1e-4
 
 
 def test_status_flags():
@@ -194,6 +227,30 @@ def test_status_flags():
     d.set_populations(big)
     d.step(1)
     assert d.sync_status() == -5  # LBM_ERR_DOMAIN
+
+
+def test_bounded_wait_runs_out_and_the_context_recovers():
+    """Failure detection without a fault: the fused kernel's first wait for a
+    population tensor copy (block 0) is made on a barrier that nothing
+    completes, bounded by 1 ms.  The wait gives up, the block drains its own
+    copy in flight and returns, and the status word reports LBM_ERR_TIMEOUT;
+    after the state is set again the next steps run clean and match the
+    steps of an untouched context bit for bit."""
+    case = build("droplet_tiles")  # 40-wide rows: the tensor-copy path
+    f = oracle_init(case).float()
+    d = gpu(case)
+    d.set_populations(f)
+    d.inject_wait_timeout()
+    d.step(1)
+    assert d.sync_status() == -7  # LBM_ERR_TIMEOUT
+    d.set_populations(f)  # clears the flag
+    d.step(3)
+    assert d.sync_status() == 0
+    ref = gpu(case)
+    ref.set_populations(f)
+    ref.step(3)
+    assert ref.sync_status() == 0
+    assert torch.equal(d.get_state(), ref.get_state())
 
 
 def test_raw_state_roundtrip_and_determinism():

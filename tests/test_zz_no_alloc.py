@@ -19,7 +19,11 @@ pytestmark = pytest.mark.gpu
 TOL = 2e-6  # the per-step population tolerance of the parity tests
 
 
-@pytest.mark.parametrize("name", ["wall_phi", "droplet_periodic"])
+# wall_phi (11-wide rows) and droplet_periodic (13-wide) take the fused
+# kernel's per-thread-load path; droplet_tiles (40-wide, all fluid: the
+# mask-free instantiation) and wall_tiles (36-wide, walls) its tensor-copy
+# path.  All have at most LBM_NOALLOC_MAX_NODES nodes.
+@pytest.mark.parametrize("name", ["wall_phi", "droplet_periodic", "droplet_tiles", "wall_tiles"])
 def test_noalloc_step_matches_regular_entry_points(name):
     case = build(name)
     nx, ny, nz = case["n"]
@@ -54,3 +58,18 @@ def test_noalloc_rejects_oversized_domain_and_aliasing():
     assert Bd.step_noalloc(f, g, None, case["p"]) == Bd.LBM_ERR_SIZE
     h = torch.zeros(27, 4, 4, 4, device="cuda")
     assert Bd.step_noalloc(h, h, None, case["p"]) == Bd.LBM_ERR_ARG
+
+
+def test_noalloc_reports_a_non_finite_state():
+    """The step's status word is read back: a NaN population in f_in gives
+    LBM_ERR_NONFINITE, and the next clean call returns LBM_OK again."""
+    case = build("droplet_tiles")
+    p = case["p"]
+    p.shift_mode = Bd.SHIFT_CONST
+    p.rho_shift = 0.0
+    f0 = oracle_init(case).float().contiguous().cuda()
+    bad = f0.clone()
+    bad[:, 3, 4, 5] = float("nan")
+    out = torch.empty_like(f0)
+    assert Bd.step_noalloc(bad, out, None, p) == Bd.LBM_ERR_NONFINITE
+    assert Bd.step_noalloc(f0, out, None, p) == Bd.LBM_OK
