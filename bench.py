@@ -384,6 +384,59 @@ def run_adjoint(local, n: int, T: int, K: int = 100):
     return out
 
 
+WETTING_SETUP = ("drop on a wall: 64x64x40, solid planes z=0 and z=39, hemisphere R=18 (tanh width 5) on the "
+                 "wall plane z=0.5, vdW a=9/392 b=2/21 T=0.8Tc kappa=0.02, rates 1; angle from a sphere fit to the "
+                 "mid-density surface after 10000 steps")
+
+
+def wetting_table(local, steps: int = 10000, iters: int = 9):
+    """Contact angle against the wetting parameter (Eq. 38): the wetting value
+    that gives each target angle, by bisection on phi (below 90 degrees) or
+    delta_rho (above), and the angle the calibrated value gives after twice
+    the steps."""
+    import numpy as np
+    import torch
+
+    from oracle import thermo as T
+    from paper_2504_03819_gb300 import Domain, Params
+    from paper_2504_03819_gb300 import inputs as I
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _wetting import contact_angle
+    nx, ny, nz, R = 64, 64, 40, 18.0
+    eos = T.at_reduced_temperature(9.0 / 392.0, 2.0 / 21.0, 1.0, 0.8)
+    rl, rv = T.maxwell(eos)
+    mask = I.wall_mask(nx, ny, nz, planes=(0, nz - 1))
+    rho0 = torch.from_numpy(I.sessile_droplet(nx, ny, nz, R, rl, rv, wall_z=0.5).astype(np.float32))
+
+    def angle(mode, value, n=steps):
+        p = Params(a=eos.a, b=eos.b, R=eos.R, T=eos.T, kappa=0.02, rho_l=rl, rho_v=rv, wetting_mode=mode,
+                   wetting_value=value)
+        d = Domain(nx, ny, nz, "f32", solid_mask=mask, device=f"cuda:{local}")
+        d.set_params(p)
+        d.set_state(rho0)
+        d.step(n)
+        st = d.sync_status()
+        th = contact_angle(d.moments()["rho"].double().cpu().numpy(), rl, rv, mask.astype(bool)) if st == 0 \
+            else float("nan")
+        d.close()
+        return th
+
+    rows = [{"target_deg": 90.0, "mode": "neutral", "value": 0.0, "angle_deg": angle(0, 0.0),
+             "angle_deg_2x_steps": angle(0, 0.0, 2 * steps)}]
+    for target, mode, lo, hi in ((60.0, 1, 1.0, 1.4), (30.0, 1, 1.0, 1.4), (120.0, 2, 0.0, 1.2), (150.0, 2, 0.0, 1.2)):
+        for _ in range(iters):  # phi lowers the angle, delta_rho raises it
+            mid = 0.5 * (lo + hi)
+            th = angle(mode, mid)
+            if (th > target) == (mode == 1):
+                lo = mid
+            else:
+                hi = mid
+        v = 0.5 * (lo + hi)
+        rows.append({"target_deg": target, "mode": "phi" if mode == 1 else "delta_rho", "value": v,
+                     "angle_deg": angle(mode, v), "angle_deg_2x_steps": angle(mode, v, 2 * steps)})
+    return {"setup": WETTING_SETUP, "rows": rows}
+
+
 def cpu_sample(nx: int, ny: int, nz: int, nsteps: int):
     """Time the FP64 oracle (as it stands) on a z-slab of the workload."""
     import numpy as np
@@ -499,11 +552,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the MLUPS of the other workload configurations")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--wetting-table", action="store_true",
+                    help="print the contact angle calibration (wetting value for 30/60/90/120/150 degrees) and exit")
     ap.add_argument("--sustain-s", type=float, default=SUSTAIN_S,
                     help="seconds of the sustained region after the repeats (0: none)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.wetting_table:
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(wetting_table(0)))
         return
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()

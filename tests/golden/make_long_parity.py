@@ -19,7 +19,7 @@ sys.path.insert(0, HERE)
 import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
-from long_cases import EOS, LONG_CASES, STEPS  # noqa: E402
+from long_cases import LONG_CASES, STEPS, eos_of  # noqa: E402
 from oracle import step as S  # noqa: E402
 from oracle import thermo as T  # noqa: E402
 from paper_2504_03819_gb300 import inputs as I  # noqa: E402
@@ -39,6 +39,7 @@ def inputs(c, rl, rv):
 
 def run(name):
     c = LONG_CASES[name]
+    EOS = eos_of(c)
     eos = T.at_reduced_temperature(EOS["a"], EOS["b"], EOS["R"], EOS["t_over_tc"])
     rl, rv = T.maxwell(eos)
     om = [1.0] * 11

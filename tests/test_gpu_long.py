@@ -90,8 +90,9 @@ def _long_case(name: str):
     import os
     import sys
     sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
-    from long_cases import EOS, LONG_CASES
+    from long_cases import LONG_CASES, eos_of
     c = LONG_CASES[name]
+    EOS = eos_of(c)
     om = [1.0] * 11
     om[1] = c["omega1"]
     p = vdw(EOS["a"], EOS["t_over_tc"], EOS["kappa"], omega=om, wetting_mode=c["wetting_mode"],
@@ -108,12 +109,12 @@ def _long_case(name: str):
     return c, p, rho0.astype(np.float32), u0.astype(np.float32), mask, ref
 
 
-@pytest.mark.parametrize("name", ["droplet24", "moving24", "wall32"])
+@pytest.mark.parametrize("name", ["droplet24", "moving24", "wall32p"])
 @pytest.mark.parametrize("storage,rho_tol,u_tol", [("f32", 1e-5, 1e-6), ("f16", 1e-3, None)])
 def test_workload_copies_thousand_steps(name, storage, rho_tol, u_tol):
     """Scaled copies of the stationary droplet, the moving droplet (omega_1 =
-    1.6, U = (0.05, 0.02, 0)) and the droplet on a phi-wetting wall
-    (tests/golden/long_cases.py) after 1000 steps against the FP64 oracle's
+    1.6, U = (0.05, 0.02, 0)) and the droplet on a phi-wetting wall (paper
+    EOS at 0.8 T_c; tests/golden/long_cases.py) after 1000 steps against the FP64 oracle's
     fields written by tests/golden/make_long_parity.py: the method's
     precision contract (FP32 storage: relative density 1e-5, |du| 1e-6; FP16
     storage: relative density 1e-3) on the fluid nodes, and the fluid mass."""
