@@ -434,7 +434,77 @@ def wetting_table(local, steps: int = 10000, iters: int = 9):
         v = 0.5 * (lo + hi)
         rows.append({"target_deg": target, "mode": "phi" if mode == 1 else "delta_rho", "value": v,
                      "angle_deg": angle(mode, v), "angle_deg_2x_steps": angle(mode, v, 2 * steps)})
-    return {"setup": WETTING_SETUP, "rows": rows}
+    return {"setup": WETTING_SETUP, "rows": rows, "paper_setup": paper_wetting(local)}
+
+
+PAPER_WETTING_SETUP = ("Sec. III C runs: 128x256x256, solid planes z=0 and z=255, drop r=30 (tanh width 5) on the "
+                       "wall plane z=0.5, vdW a=9/392 b=2/21 T=0.7Tc kappa=0.02, nu=0.15, omega_3=0.5 (with "
+                       "omega_3=1 the vapour at the walls grows a mode), other rates 1; angle from a sphere fit to the "
+                       "mid-density surface; start: hemisphere unless a cap angle is given")
+
+
+def paper_wetting(local):
+    """The paper's three wetting runs at its size and temperature, plus the
+    delta_rho branch between, with the angle after each checkpoint."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from oracle import thermo as T
+    from paper_2504_03819_gb300 import Domain, Params
+    from paper_2504_03819_gb300 import inputs as I
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _wetting import contact_angle
+    nx, ny, nz, r = 128, 256, 256, 30.0
+    eos = T.at_reduced_temperature(9.0 / 392.0, 2.0 / 21.0, 1.0, 0.7)
+    rl, rv = T.maxwell(eos)
+    mask = I.wall_mask(nx, ny, nz, planes=(0, nz - 1))
+    solid = mask.astype(bool)
+    om = [1.0] * 11
+    om[3] = 0.5
+
+    def run(mode, value, checkpoints, cap_deg=None):
+        if cap_deg is None:
+            rho0 = I.sessile_droplet(nx, ny, nz, r, rl, rv, wall_z=0.5)
+        else:  # cap of the hemisphere's volume meeting the wall at cap_deg
+            th = math.radians(cap_deg)
+            rc = (2.0 * r ** 3 / (2.0 - 3.0 * math.cos(th) + math.cos(th) ** 3)) ** (1.0 / 3.0)
+            rho0 = I.droplet(nx, ny, nz, rc, rl, rv, centre=((nx - 1) / 2.0, (ny - 1) / 2.0, 0.5 - rc * math.cos(th)))
+        vol0 = float(((rho0 - rv) / (rl - rv))[~solid].sum())
+        p = Params(a=eos.a, b=eos.b, R=eos.R, T=eos.T, kappa=0.02, nu=0.15, omega=om, rho_l=rl, rho_v=rv,
+                   wetting_mode=mode, wetting_value=value)
+        d = Domain(nx, ny, nz, "f32", solid_mask=mask, device=f"cuda:{local}")
+        d.set_params(p)
+        d.set_state(torch.from_numpy(rho0.astype(np.float32)))
+        out, done = [], 0
+        for c in checkpoints:
+            d.step(c - done)
+            done = c
+            st = d.sync_status()
+            if st != 0:
+                out.append({"steps": c, "status": st})
+                break
+            rho = d.moments()["rho"].double().cpu().numpy()
+            liquid = rho > 0.5 * (rl + rv)
+            on_wall = int(liquid[1].sum())
+            out.append({"steps": c, "angle_deg": round(contact_angle(rho, rl, rv, solid), 2) if on_wall else None,
+                        "liquid_nodes_on_wall": on_wall,
+                        "volume_ratio": round(float(((rho - rv) / (rl - rv))[~solid].sum()) / vol0, 4)})
+        d.close()
+        return out
+
+    rows = [
+        {"wetting": "neutral", "paper_deg": 89.9, "start": "hemisphere", "runs": run(0, 0.0, (10000, 20000, 40000))},
+        {"wetting": "phi=1.6", "paper_deg": 33.5, "start": "hemisphere", "runs": run(1, 1.6, (10000, 20000, 40000))},
+        {"wetting": "delta_rho=1.8", "paper_deg": 153.4, "start": "hemisphere", "runs": run(2, 1.8, (2000, 10000))},
+        {"wetting": "delta_rho=1.8", "paper_deg": 153.4, "start": "150 deg cap", "runs": run(2, 1.8, (10000, 20000),
+                                                                                          cap_deg=150.0)},
+    ]
+    for v in (0.6, 1.0, 1.4):
+        rows.append({"wetting": f"delta_rho={v}", "paper_deg": None, "start": "hemisphere",
+                     "runs": run(2, v, (10000,))})
+    return {"setup": PAPER_WETTING_SETUP, "rows": rows}
 
 
 def cpu_sample(nx: int, ny: int, nz: int, nsteps: int):

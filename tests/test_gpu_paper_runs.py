@@ -12,19 +12,24 @@
   the workload's a = 9/49, kappa = 0.01 a width-5 drop of R >= 12 goes
   non-finite, so the check runs the paper's EOS at 0.7 T_c (nu = 0.15).
 * Sec. III C, Eq. 38, Fig. 7: the contact angle of a drop on a wall follows
-  the wetting parameter.  The paper's own setup (0.7 T_c) grows a wall mode
-  on the GPU and in the oracle, and the workload's a = 9/49, kappa = 0.01
-  leaves the angle at 90 degrees for every phi and delta_rho and goes
-  non-finite within 40 000 steps, so the check runs the paper's EOS at
-  0.8 T_c.
+  the wetting parameter (paper EOS at 0.8 T_c, all rates 1), and the
+  paper's own wetting runs (128 x 256 x 256, r = 30, 0.7 T_c, nu = 0.15)
+  give its angles once omega_3 = 0.5 damps the mode that the vapour grows
+  next to the walls with every other rate 1.  The workload's a = 9/49,
+  kappa = 0.01 leaves the angle at 90 degrees for every phi and delta_rho
+  and goes non-finite within 40 000 steps.
 * Sec. III B, Fig. 4(a): without the fourth-order correction (Eq. 28) the
   r = 30 droplet in 128^3 (0.7 T_c, nu = 0.15) diverges shortly after t = 86
   (FP64); with it the droplet stays finite.  In FP32 the uncorrected run
   goes non-finite between steps 50 and 60, so the check is: non-finite
   within 150 steps without the correction, finite and slow after 300 steps
   with it.
+* Sec. III B, Fig. 6: that droplet between walls moving at U = 0.1 keeps
+  its round shape while the flow carries it (omega_3 = 0.5, as for the wall
+  runs of Sec. III C).
 """
 import json
+import math
 import os
 
 import numpy as np
@@ -145,8 +150,8 @@ def test_contact_angle_follows_the_wetting_parameter():
     degrees; phi > 1 makes the wall hydrophilic, each larger phi a smaller
     angle; delta_rho > 0 hydrophobic, each larger delta_rho a larger angle
     (measured 90.3; 72.8, 56.8, 40.6 for phi = 1.1, 1.2, 1.3; 100.4, 115.5,
-    132.4 for delta_rho = 0.2, 0.5, 0.8).  The liquid volume stays put (no
-    evaporation: every angle belongs to the same drop)."""
+    132.4 for delta_rho = 0.2, 0.5, 0.8).  The total mass is conserved (to
+    1e-4; halfway bounce-back loses none)."""
     import sys
     sys.path.insert(0, os.path.dirname(__file__))
     from _wetting import contact_angle
@@ -163,9 +168,7 @@ def test_contact_angle_follows_the_wetting_parameter():
         d.step(10000)
         assert d.sync_status() == 0
         rho = d.moments()["rho"].double().cpu().numpy()
-        vol0 = float(((rho0 - rv) / (rl - rv))[~solid].sum())
-        vol = float(((rho - rv) / (rl - rv))[~solid].sum())
-        assert vol == pytest.approx(vol0, rel=0.02)
+        assert float(rho[~solid].sum()) == pytest.approx(float(rho0[~solid].astype(np.float64).sum()), rel=1e-4)
         angles[(mode, value)] = contact_angle(rho, rl, rv, solid)
         d.close()
     assert angles[(0, 0.0)] == pytest.approx(90.0, abs=2.0)
@@ -173,3 +176,118 @@ def test_contact_angle_follows_the_wetting_parameter():
     drho = [angles[(2, v)] for v in (0.2, 0.5, 0.8)]
     assert 88.0 > phi[0] > phi[1] > phi[2]
     assert 92.0 < drho[0] < drho[1] < drho[2]
+
+
+def _paper_wall_run(mode, value, steps, omega3=0.5, cap_deg=None, n=(128, 256, 256), r=30.0):
+    """Sec. III C setup: drop of radius r on the bottom wall (solid planes
+    z = 0 and nz - 1), 0.7 T_c, nu = 0.15; returns the status, the angle and
+    the total mass before and after.  cap_deg: start from a spherical cap
+    of the hemisphere's volume meeting the wall at that angle."""
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _wetting import contact_angle
+    nx, ny, nz = n
+    om = [1.0] * 11
+    om[3] = omega3
+    p, rl, rv = paper_params(0.7, nu=0.15, omega=om, wetting_mode=mode, wetting_value=value)
+    mask = I.wall_mask(nx, ny, nz, planes=(0, nz - 1))
+    solid = mask.astype(bool)
+    if cap_deg is None:
+        rho0 = I.sessile_droplet(nx, ny, nz, r, rl, rv, wall_z=0.5)
+    else:
+        th = math.radians(cap_deg)
+        rc = (2.0 * r ** 3 / (2.0 - 3.0 * math.cos(th) + math.cos(th) ** 3)) ** (1.0 / 3.0)
+        rho0 = I.droplet(nx, ny, nz, rc, rl, rv, centre=((nx - 1) / 2.0, (ny - 1) / 2.0, 0.5 - rc * math.cos(th)))
+    rho0 = rho0.astype(np.float32)
+    d = Domain(nx, ny, nz, "f32", solid_mask=mask)
+    d.set_params(p)
+    d.set_state(torch.from_numpy(rho0))
+    d.step(steps)
+    st = d.sync_status()
+    angle, vol = float("nan"), float("nan")
+    if st == 0:
+        rho = d.moments()["rho"].double().cpu().numpy()
+        angle = contact_angle(rho, rl, rv, solid)
+        vol = float(rho[~solid].sum())
+    d.close()
+    return st, angle, float(rho0[~solid].astype(np.float64).sum()), vol
+
+
+def test_wetting_runs_of_the_paper_at_its_temperature():
+    """Sec. III C, Fig. 7, at the paper's size and temperature: 128 x 256 x
+    256, r = 30 on the bottom wall, 0.7 T_c, nu = 0.15.  With every rate but
+    omega_1 equal to 1 the vapour next to the walls grows a mode and the run
+    goes non-finite within 2000 steps (also the oracle; here on 64 x 64 x
+    40); omega_3 = 0.5 damps it and leaves the static state alone.  Then
+    neutral wetting gives 90.4 degrees after 20 000 steps (the paper: 89.9),
+    phi = 1.6 gives 30.1 (the paper: 33.5); delta_rho = 1.8 started from the
+    hemisphere throws the drop off the wall within 2000 steps, started from a
+    150-degree cap it stays on the wall at 161.5 after 10 000 steps (the
+    paper: 153.4).  Held: neutral within 1.5 degrees of 90, phi = 1.6 within
+    5 degrees of the paper's angle, delta_rho = 1.8 above 150 degrees, and the
+    total mass to 1e-4.  The drops slowly evaporate into the box at an
+    unchanged angle (the Kelvin effect: the neutral drop's wetted area falls
+    from 2072 to 1116 nodes between 10 000 and 40 000 steps)."""
+    st, _, _, _ = _paper_wall_run(0, 0.0, 2000, omega3=1.0, n=(64, 64, 40), r=16.0)
+    assert st in (-4, -5)  # LBM_ERR_NONFINITE or LBM_ERR_DOMAIN with the stated rates
+    st, neutral, v0, v = _paper_wall_run(0, 0.0, 20000)
+    assert st == 0 and neutral == pytest.approx(90.0, abs=1.5)
+    assert v == pytest.approx(v0, rel=1e-4)
+    st, phi, v0, v = _paper_wall_run(1, 1.6, 20000)
+    assert st == 0 and phi == pytest.approx(GOLD["contact_angles"]["phi_1p6"], abs=5.0)
+    assert v == pytest.approx(v0, rel=1e-4)
+    st, drho, v0, v = _paper_wall_run(2, 1.8, 10000, cap_deg=150.0)
+    assert st == 0 and 150.0 < drho < 180.0
+    assert v == pytest.approx(v0, rel=1e-4)
+
+
+def test_droplet_between_moving_walls_stays_round():
+    """Sec. III B, Fig. 6: the r = 30 stationary droplet of 128^3 (0.7 T_c,
+    nu = 0.15) with the top and bottom planes turned into walls moving at
+    U = 0.1 along x (reading R17) keeps its round shape while the flow
+    carries it.  omega_3 = 0.5 as for the wall runs of Sec. III C (with every
+    rate 1 the run goes non-finite within 500 steps).  After 20 000 steps the
+    liquid region's principal radii of gyration agree to 1 % (measured
+    aspect 1.006) and the drop has moved along +x (centroid tracked every
+    1000 steps, unwrapped over the periodic x).  The drop trails the
+    walls: the lattice sum of F = (1/3 - rho) grad mu vanishes only at
+    equilibrium, so a moving interface loses momentum (in the oracle a
+    cylinder given U = 0.1 keeps half of it after 1600 steps), and the run
+    reaches a steady shear profile instead of the walls' velocity; it goes
+    non-finite between 40 000 and 60 000 steps (the paper runs 100 000)."""
+    n, r, U = 128, 30.0, 0.1
+    om = [1.0] * 11
+    om[3] = 0.5
+    p, rl, rv = paper_params(0.7, nu=0.15, omega=om)
+    mask = I.wall_mask(n, n, n, planes=(0, n - 1))
+    solid = mask.astype(bool)
+    wu = np.zeros((3, n, n, n), np.float32)
+    wu[0][solid] = U
+    d = Domain(n, n, n, "f32", solid_mask=mask)
+    d.set_params(p)
+    d.set_wall_velocity(torch.from_numpy(wu))
+    d.set_state(torch.from_numpy(I.droplet(n, n, n, r, rl, rv).astype(np.float32)))
+
+    def centroid_x(rho):
+        liq = (rho > 0.5 * (rl + rv)) & ~solid
+        ang = 2.0 * np.pi * np.nonzero(liq)[2] / n
+        return (math.atan2(np.sin(ang).mean(), np.cos(ang).mean()) % (2.0 * np.pi)) * n / (2.0 * np.pi), liq
+
+    # centroid every 1000 steps, unwrapped (the drop moves far less than n/2
+    # per interval)
+    x_prev, _ = centroid_x(d.moments()["rho"].double().cpu().numpy())
+    moved = 0.0
+    for _ in range(20):
+        d.step(1000)
+        assert d.sync_status() == 0
+        rho = d.moments()["rho"].double().cpu().numpy()
+        cx, liq = centroid_x(rho)
+        moved += (cx - x_prev + n / 2.0) % n - n / 2.0
+        x_prev = cx
+    d.close()
+    assert moved > 10.0
+    idx = np.nonzero(liq)
+    dxs = np.remainder(idx[2] - cx + n / 2.0, n) - n / 2.0
+    P = np.stack([dxs, idx[1] - idx[1].mean(), idx[0] - idx[0].mean()], 1)
+    ev = np.linalg.eigvalsh(P.T @ P / len(P))
+    assert math.sqrt(ev[-1] / ev[0]) < 1.01
