@@ -46,11 +46,11 @@ WORKLOAD_NAME = ("moving droplet 256^3 periodic, R=32 (tanh width 2), U=(0.05,0.
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
 # storage, valid only while the kernel sources hash to `src`.  The capture is
-# `--profile-case step128` (k_fused<float>, 128^3, 2,097,152 nodes): 289.37 MB
-# read + 194.89 MB written = 230.9 B per node, scaled by 8 to one 256^3 launch
+# `--profile-case step128` (k_fused<float>, 128^3, 2,097,152 nodes): 289.33 MB
+# read + 194.69 MB written = 230.8 B per node, scaled by 8 to one 256^3 launch
 # (the kernel's traffic is proportional to the nodes it updates).
-NCU_TRAFFIC = {"f32": {"kernel": "collide", "bytes_per_launch": 3874019328, "bytes_per_lu": 230.9,
-                       "captured_on": "128^3, scaled x8", "src": "dfa4dea67d37a322"}}
+NCU_TRAFFIC = {"f32": {"kernel": "collide", "bytes_per_launch": 3872188416, "bytes_per_lu": 230.8,
+                       "captured_on": "128^3, scaled x8", "src": "9c40bc42a9354c66"}}
 
 
 def src_hash() -> str:
@@ -576,8 +576,9 @@ def cpu_baseline():
 
 def profile_case(name: str):
     """Small runs for ncu captures (no timing): 'step128' = 4 steps of the
-    moving-droplet case on 128^3 (2.1 M nodes, state 0.23 GB > L2);
-    'adjoint64' = 4 adjoint steps of the 64^3 wall case."""
+    moving-droplet case on 128^3 (2.1 M nodes, state 0.23 GB > L2; 'step128h'
+    the same with FP16 storage); 'adjoint64' = 4 adjoint steps of the 64^3
+    wall case."""
     import numpy as np
     import torch
 
@@ -587,12 +588,12 @@ def profile_case(name: str):
     from paper_2504_03819_gb300 import inputs as I
     from paper_2504_03819_gb300.adjoint import rollout_gradient
     __graft_entry__.build()
-    if name == "step128":
+    if name in ("step128", "step128h"):
         n = 128
         om = [1.0] * 11
         om[1] = 1.6
         p = Params.vdw(9.0 / 49.0, 2.0 / 21.0, 1.0, 0.85, 0.01, omega=om)
-        d = Domain(n, n, n, "f32")
+        d = Domain(n, n, n, "f16" if name == "step128h" else "f32")
         d.set_params(p)
         d.set_state(torch.from_numpy(I.droplet(n, n, n, 16.0, p.rho_l, p.rho_v, width=2.0).astype(np.float32)),
                     torch.from_numpy(I.uniform_velocity(n, n, n, (0.05, 0.02, 0.0)).astype(np.float32)))

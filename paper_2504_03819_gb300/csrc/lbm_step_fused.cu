@@ -232,10 +232,12 @@ constexpr int S1 = (H1P + NT - 1) / NT;
 constexpr int S2 = (H2P + NT - 1) / NT;
 
 struct FusedSmem {
-  float mu[5][H2P];       // mu' planes z-2 .. z+2 (two-node ring)
+  float mu[4][H2P];       // mu' planes z-1 .. z+2 (two-node ring)
   float rho[4][H1P];      // rho planes z-2 .. z+1 (one-node ring)
-  float j[4][3][H1P];     // j planes
-  float phi[3][3][H1P];   // (p_m - rho/3) u planes z-1 .. z+1
+  float j[3][3][H1P];     // j planes
+  float gp[2][3][H1P];    // per ring position: the mu' partial sums of the gradient (two planes)
+  float phi[3][H1P];      // (p_m - rho/3) u of the newest plane
+  float qp[2][3][NT];     // per tile node: the phi partial sums of Q (planes z-1, z)
   float shift[3][4][H1P]; // storage shift by speed class, planes z-1 .. z+1
   float uF[2][6][NT];     // u, F of the tile for planes z, z+1
   uint8_t solid[4][H1P];  // mask planes
@@ -249,7 +251,6 @@ template <typename T> constexpr size_t fused_smem_size(bool tma) {
   return tma ? FBUF_OFFSET + 27 * NT * sizeof(T) : sizeof(FusedSmem);
 }
 
-__device__ __forceinline__ int r5(int z) { return (z + 10) % 5; }  // z >= -2
 __device__ __forceinline__ int r4(int z) { return (z + 8) & 3; }
 __device__ __forceinline__ int r3(int z) { return (z + 6) % 3; }
 __device__ __forceinline__ int r2(int z) { return (z + 4) & 1; }
@@ -273,6 +274,13 @@ struct MomArgs {
   int zspan;  // one block's z range is the whole domain
 };
 
+// Base address of each population's plane of the output state (fout + q N):
+// kernel parameters, so every push store is one constant-bank base plus the
+// 32-bit node index of its destination.
+template <typename T> struct PopPlanes {
+  T *p[27];
+};
+
 template <typename T> __device__ __forceinline__ float to_f32(T v);
 template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
 template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     k_fused(const T *__restrict__ fin, T *__restrict__ fout, const uint8_t *__restrict__ mask,
             const float *__restrict__ rho, const float *__restrict__ jv, const float *__restrict__ mu,
             const float *sb, float *sb_out, int *__restrict__ status, float *__restrict__ cap,
-            const float *__restrict__ wall_u, MomArgs mo, KParams kp, int TZ,
+            const float *__restrict__ wall_u, MomArgs mo, const PopPlanes<T> op, KParams kp, int TZ,
             const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
@@ -360,20 +368,20 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       if (MASK) psolid[s] = (ok && mask) ? mask[g] : (uint8_t)0;
     }
   };
-  auto store = [&](int s5, int zr) {  // s5: ring slot of the mu' plane
-    float *dm = S.mu[s5];
+  auto store = [&](int s4, int zr) {  // s4: ring slot of the mu' plane
+    float *dm = S.mu[s4];
 #pragma unroll
     for (int s = 0; s < S2; ++s)
       if (tid + s * NT < H2P) dm[tid + s * NT] = pmu[s];
-    const int rg = r4(zr);
+    const int rg = r4(zr), jg = r3(zr);
 #pragma unroll
     for (int s = 0; s < S1; ++s) {
       const int k = tid + s * NT;
       if (k < H1P) {
         S.rho[rg][k] = prho[s];
-        S.j[rg][0][k] = pj[0][s];
-        S.j[rg][1][k] = pj[1][s];
-        S.j[rg][2][k] = pj[2][s];
+        S.j[jg][0][k] = pj[0][s];
+        S.j[jg][1][k] = pj[1][s];
+        S.j[jg][2][k] = pj[2][s];
         if (MASK) S.solid[rg][k] = psolid[s];
       }
     }
@@ -390,42 +398,66 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     fc[s] = (hy + 1) * H2X + hx + 1;
     ft[s] = (hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) ? (hy - 1) * TX + hx - 1 : -1;
   }
-  // (a5m, a5, a5p: ring slots of mu' planes z-1 .. z+1; rp: slot of plane z
-  // in the three-plane rings)
-  auto fields = [&](int z, bool keep_uF, int a5m, int a5, int a5p, int rp) {
-    const int rg = r4(z);
-    const float *m0 = S.mu[a5m], *m1 = S.mu[a5], *m2 = S.mu[a5p];
+  // The gradient of Eq. 12, sum_q w_q c_q mu'(x + c_q), factored like Q
+  // (w_q = w1(cx) w1(cy) w1(cz)): with the in-plane partial sums of plane z'
+  //   dx(z') = sum_cy w1(cy) [mu'(x+1, y+cy) - mu'(x-1, y+cy)],
+  //   dy(z') likewise along y, pp(z') = sum_cx,cy w1(cx) w1(cy) mu',
+  // its components are w1(1) sum_cz w1(cz) dx(z+cz), likewise for y, and
+  // w1(1) (pp(z+1) - pp(z-1)).  Each thread forms the partial sums of its
+  // own ring positions once per plane, when the plane arrives, and keeps two
+  // older planes in its slots of gp.
+  auto gpart = [&](const float *mp, int c, float &dx, float &dy, float &pp) {
+    const float a = mp[c - H2X - 1], b = mp[c - H2X], e = mp[c - H2X + 1];
+    const float d = mp[c - 1], m = mp[c], g = mp[c + 1];
+    const float h = mp[c + H2X - 1], i = mp[c + H2X], l = mp[c + H2X + 1];
+    dx = fmaf(w1(0), g - d, w1(1) * ((e - a) + (l - h)));
+    dy = fmaf(w1(0), i - b, w1(1) * ((h - a) + (l - e)));
+    pp = fmaf(w1(0), fmaf(w1(0), m, w1(1) * (d + g)),
+              w1(1) * (fmaf(w1(0), b, w1(1) * (a + e)) + fmaf(w1(0), i, w1(1) * (h + l))));
+  };
+  auto gpart_store = [&](const float *mp, int zp) {
+    for (int k = tid, s = 0; k < H1P; k += NT, ++s) {
+      float dx, dy, pp;
+      gpart(mp, s ? fc[1] : fc[0], dx, dy, pp);
+      S.gp[zp & 1][0][k] = dx;
+      S.gp[zp & 1][1][k] = dy;
+      S.gp[zp & 1][2][k] = pp;
+    }
+  };
+  // (a4, a4p: ring slots of mu' planes z and z+1; rp: slot of plane z in the
+  // three-plane rings)
+  auto fields = [&](int z, bool keep_uF, int a4, int a4p, int rp) {
+    const int rg = r4(z), jg = r3(z);
+    const float *m1 = S.mu[a4], *m2 = S.mu[a4p];
+    float *gm = S.gp[(z - 1) & 1][0];  // plane z-1, then z+1
+    const float *g0 = S.gp[z & 1][0];
 #pragma unroll 1
     for (int k = tid, s = 0; k < H1P; k += NT, ++s) {
       const int fcs = s ? fc[1] : fc[0], fts = s ? ft[1] : ft[0];
       float phx = 0.0f, phy = 0.0f, phz = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f, Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
       float sh0 = 0.0f, sh1 = 0.0f, sh2 = 0.0f, sh3 = 0.0f;
+      // partial sums of plane z+1 (every position: a solid one here may be
+      // fluid in the next planes), those of z-1 replaced by them
+      float dxn, dyn, ppn;
+      gpart(m2, fcs, dxn, dyn, ppn);
+      const float dxm = gm[k], dym = gm[H1P + k], ppm = gm[2 * H1P + k];
+      gm[k] = dxn;
+      gm[H1P + k] = dyn;
+      gm[2 * H1P + k] = ppn;
       if (!MASK || !S.solid[rg][k]) {
-        const int c = fcs;  // position in the two-node ring
-        const float mc = m1[c];
-        // sum_q w_q c_q mu'(x + c_q), one partial sum per plane and axis so
-        // the dependent chains stay short (sum_q w_q c_q = 0: the centre
-        // term drops out, and mu' is a small deviation, so no centring)
-        float gx[3] = {0.0f, 0.0f, 0.0f}, gy[3] = {0.0f, 0.0f, 0.0f}, gz[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int q = 0; q < 27; ++q) {
-          if (q == 13) continue;
-          const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
-          const float *pl = cz < 0 ? m0 : (cz == 0 ? m1 : m2);
-          const float v = pl[c + cx + cy * H2X];
-          if (cx) gx[cz + 1] = fmaf(cx * weight_of(q), v, gx[cz + 1]);
-          if (cy) gy[cz + 1] = fmaf(cy * weight_of(q), v, gy[cz + 1]);
-          if (cz) gz[cz + 1] = fmaf(cz * weight_of(q), v, gz[cz + 1]);
-        }
+        const float mc = m1[fcs];
+        const float gx = w1(1) * fmaf(w1(0), g0[k], w1(1) * (dxm + dxn));
+        const float gy = w1(1) * fmaf(w1(0), g0[H1P + k], w1(1) * (dym + dyn));
+        const float gz = w1(1) * (ppn - ppm);
         const float r = S.rho[rg][k];
         const float cf = 3.0f * (1.0f / 3.0f - r);
-        Fx = cf * ((gx[0] + gx[2]) + gx[1]);
-        Fy = cf * ((gy[0] + gy[2]) + gy[1]);
-        Fz = cf * (gz[0] + gz[2]);
+        Fx = cf * gx;
+        Fy = cf * gy;
+        Fz = cf * gz;
         const float ir = 1.0f / r;
-        ux = (S.j[rg][0][k] + 0.5f * Fx) * ir;
-        uy = (S.j[rg][1][k] + 0.5f * Fy) * ir;
-        uz = (S.j[rg][2][k] + 0.5f * Fz) * ir;
+        ux = (S.j[jg][0][k] + 0.5f * Fx) * ir;
+        uy = (S.j[jg][1][k] + 0.5f * Fy) * ir;
+        uz = (S.j[jg][2][k] + 0.5f * Fz) * ir;
         const float e = basis_c(r, mc, kp);
         phx = e * ux;
         phy = e * uy;
@@ -437,9 +469,9 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
           sh3 = shift_rest(0, r, e);
         }
       }
-      S.phi[rp][0][k] = phx;
-      S.phi[rp][1][k] = phy;
-      S.phi[rp][2][k] = phz;
+      S.phi[0][k] = phx;
+      S.phi[1][k] = phy;
+      S.phi[2][k] = phz;
       if (rest) {
         S.shift[rp][0][k] = sh0;
         S.shift[rp][1][k] = sh1;
@@ -466,30 +498,71 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   const int oy[3] = {y == 0 ? (ny - 1) * nx : -nx, 0, y == ny - 1 ? -(ny - 1) * nx : nx};
 
   // prologue: mu' planes z0-2 .. z0+1 and rho/j planes z0-1 .. z0 in shared
-  // memory, mu'(z0+2) and rho/j(z0+1) in registers; phi of z0-1 and z0,
-  // u/F of z0
+  // memory, mu'(z0+2) and rho/j(z0+1) in registers; the gradient partial
+  // sums of z0-2 .. z0+1, phi of z0-1 and z0, u/F of z0.  mu'(z0-2) takes the
+  // slot of z0+2: its partial sums are formed before that plane is stored.
   fetch(z0 - 2, z0 - 1);
-  store(r5(z0 - 2), z0 - 1);
+  store(r4(z0 - 2), z0 - 1);
   fetch(z0 - 1, z0);
-  store(r5(z0 - 1), z0);
+  store(r4(z0 - 1), z0);
   fetch(z0, z0);
-  store(r5(z0), z0);
+  store(r4(z0), z0);
   fetch(z0 + 1, z0);
-  store(r5(z0 + 1), z0);
-  fetch(z0 + 2, z0 + 1);
+  store(r4(z0 + 1), z0);
   __syncthreads();
-  fields(z0 - 1, false, r5(z0 - 2), r5(z0 - 1), r5(z0), r3(z0 - 1));
-  fields(z0, true, r5(z0 - 1), r5(z0), r5(z0 + 1), r3(z0));
-
+  gpart_store(S.mu[r4(z0 - 2)], z0 - 2);
+  gpart_store(S.mu[r4(z0 - 1)], z0 - 1);
+  fetch(z0 + 2, z0 + 1);
   const int c1 = (ty + 1) * H1X + tx + 1;
-  // ring slots of planes z, z+1, z+2 (mu') and z-1, z, z+1 (phi, shift),
+  const int t = ty * TX + tx;
+  // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa phi_a(x + c_q) (Eq. 27).  The
+  // weights factor, w_q = w1(cx) w1(cy) w1(cz), so with the in-plane partial
+  // sums of plane z'
+  //   ex(z') = sum_cy w1(cy) [phi_x(x+1, y+cy) - phi_x(x-1, y+cy)],
+  //   ey(z') likewise along y, pz(z') = sum_cx,cy w1(cx) w1(cy) phi_z,
+  // Q_x = -9/6 sum_cz w1(cz) ex(z+cz), Q_y likewise, Q_z = -9/6 (pz(z+1) -
+  // pz(z-1)).  Each thread forms the partial sums of its own node once per
+  // plane, right after the plane's phi, and keeps the two older planes in
+  // its slots of qp.
+  auto qpartials = [&](int zp, float &ex_out, float &ey_out, float &pz_out) {
+    const float *px = S.phi[0], *py = S.phi[1], *pz = S.phi[2];
+    const float ex = fmaf(w1(0), px[c1 + 1] - px[c1 - 1],
+                          w1(1) * ((px[c1 + 1 - H1X] - px[c1 - 1 - H1X]) + (px[c1 + 1 + H1X] - px[c1 - 1 + H1X])));
+    const float ey = fmaf(w1(0), py[c1 + H1X] - py[c1 - H1X],
+                          w1(1) * ((py[c1 + H1X - 1] - py[c1 - H1X - 1]) + (py[c1 + H1X + 1] - py[c1 - H1X + 1])));
+    float row[3];
+#pragma unroll
+    for (int cy = -1; cy <= 1; ++cy) {
+      const int o = c1 + cy * H1X;
+      row[cy + 1] = fmaf(w1(0), pz[o], w1(1) * (pz[o - 1] + pz[o + 1]));
+    }
+    const float pzs = fmaf(w1(0), row[1], w1(1) * (row[0] + row[2]));
+    float *dst = S.qp[zp & 1][0];
+    dst[t] = ex;
+    dst[NT + t] = ey;
+    dst[2 * NT + t] = pzs;
+    ex_out = ex;
+    ey_out = ey;
+    pz_out = pzs;
+  };
+  float qdummy[3];
+
+  __syncthreads();
+  fields(z0 - 1, false, r4(z0 - 1), r4(z0), r3(z0 - 1));
+  __syncthreads();
+  qpartials(z0 - 1, qdummy[0], qdummy[1], qdummy[2]);
+  __syncthreads();  // the phi plane is rewritten next
+  fields(z0, true, r4(z0), r4(z0 + 1), r3(z0));
+  __syncthreads();
+  qpartials(z0, qdummy[0], qdummy[1], qdummy[2]);
+  // ring slots of planes z, z+1, z+2 (mu') and z-1, z, z+1 (shift),
   // carried from plane to plane instead of recomputed (no division)
-  int i5a = r5(z0), i5b = r5(z0 + 1), i5c = r5(z0 + 2);
+  int i5a = r4(z0), i5b = r4(z0 + 1), i5c = r4(z0 + 2);
   int i3m = r3(z0 - 1), i3a = r3(z0), i3b = r3(z0 + 1);
   auto advance = [&]() {
     i5a = i5b;
     i5b = i5c;
-    i5c = i5c == 4 ? 0 : i5c + 1;
+    i5c = (i5c + 1) & 3;
     const int t = i3m;
     i3m = i3a;
     i3a = i3b;
@@ -498,26 +571,8 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
 
   // corrections, collision and push of fluid node n of plane z (its
   // populations in f, the shift basis of its stored state in rb, cb)
-  auto update = [&](int z, int n, float (&f)[27], float rb, float cb) {
-    // Q_aa = -3 d_a phi_a = -9 sum_q w_q c_qa phi_a(x + c_q), partial sums
-    // per plane
-    const float *p0 = S.phi[i3m][0], *p1 = S.phi[i3a][0], *p2 = S.phi[i3b][0];
-    float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f}, qz[2] = {0.0f, 0.0f};
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      if (q == 13) continue;
-      const int cx = cx_of(q), cy = cy_of(q), cz = cz_of(q);
-      const float *pl = cz < 0 ? p0 : (cz == 0 ? p1 : p2);
-      const int o = c1 + cx + cy * H1X;
-      if (cx) qx[cz + 1] = fmaf(cx * weight_of(q), pl[o], qx[cz + 1]);
-      if (cy) qy[cz + 1] = fmaf(cy * weight_of(q), pl[H1P + o], qy[cz + 1]);
-      if (cz) qz[cz > 0] = fmaf(cz * weight_of(q), pl[2 * H1P + o], qz[cz > 0]);
-    }
-    const float Qx = -9.0f * ((qx[0] + qx[2]) + qx[1]);
-    const float Qy = -9.0f * ((qy[0] + qy[2]) + qy[1]);
-    const float Qz = -9.0f * (qz[0] + qz[1]);
+  auto update = [&](int z, int n, float (&f)[27], float rb, float cb, float Qx, float Qy, float Qz) {
     const float *uF = S.uF[r2(z)][0];
-    const int t = ty * TX + tx;
     const float ux = uF[t], uy = uF[NT + t], uz = uF[2 * NT + t];
     const float Fx = uF[3 * NT + t], Fy = uF[4 * NT + t], Fz = uF[5 * NT + t];
     const float r_own = S.rho[r4(z)][c1];
@@ -564,7 +619,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
       float sh = weight_of(q) * kp.rho_shift;
       if (q == 13) {
         if (rest) sh = shift_rest(q, r_own, c_own);
-        store_pop<T>(fout + q * N + n, f[q] - sh);
+        store_pop<T>(op.p[q] + n, f[q] - sh);
         continue;
       }
       const int hk = c1 + cx + cy * H1X;
@@ -574,11 +629,11 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
           const int b = n + ox[cx + 1] + oy[cy + 1] + oz[cz + 1];
           sh += wall_odd(q, r_own, pm, wall_u[b], wall_u[N + b], wall_u[2 * N + b]);
         }
-        store_pop<T>(fout + (size_t)(26 - q) * N + n, f[q] - sh);
+        store_pop<T>(op.p[26 - q] + n, f[q] - sh);
       } else {
         if (rest) sh = S.shift[cz < 0 ? i3m : (cz == 0 ? i3a : i3b)][cx * cx + cy * cy + cz * cz][hk];
         const int m = n + ox[cx + 1] + oy[cy + 1] + oz[cz + 1];
-        store_pop<T>(fout + q * N + m, f[q] - sh);
+        store_pop<T>(op.p[q] + m, f[q] - sh);
       }
     }
     if (rest) {
@@ -676,10 +731,20 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
         __syncthreads();
       }
       if (!dead) {
-        fields(z + 1, true, i5a, i5b, i5c, i3b);
+        fields(z + 1, true, i5b, i5c, i3b);
         __syncthreads();
+        // Q of plane z from the partial sums of planes z-1, z (kept) and
+        // z+1 (formed now, into the slot of z-1)
+        const float *qm = S.qp[(z - 1) & 1][0], *q0 = S.qp[z & 1][0];
+        const float exm = qm[t], eym = qm[NT + t], pzm = qm[2 * NT + t];
+        const float ex0 = q0[t], ey0 = q0[NT + t];
+        float exn, eyn, pzn;
+        qpartials(z + 1, exn, eyn, pzn);
+        const float Qx = -1.5f * fmaf(w1(0), ex0, w1(1) * (exm + exn));
+        const float Qy = -1.5f * fmaf(w1(0), ey0, w1(1) * (eym + eyn));
+        const float Qz = -1.5f * (pzn - pzm);
         if (active) {
-          update(z, n, f, rb, cb);
+          update(z, n, f, rb, cb, Qx, Qy, Qz);
         } else if (cap && inside) {  // solid node: its wetting rho and mu', no flow
           cap[n] = S.rho[r4(z)][c1];
           cap[N + n] = S.mu[i5a][(ty + 2) * H2X + tx + 2];
@@ -948,6 +1013,8 @@ bool launch_fused_u(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map,
   float *sb_out = ctx->sb_out ? ctx->sb_out : d.sb;
   const uint8_t *mask = MASK ? ctx->mask : nullptr;
   const float *wall_u = WALLV ? ctx->wall_u : nullptr;
+  PopPlanes<T> op;
+  for (int q = 0; q < 27; ++q) op.p[q] = fout + (size_t)q * kp.N;
   if (TMA && produce) {
     const Moments &m = ctx->mom[1 - ctx->cur];
     MomArgs mo{m.rho, m.j, m.mu0, ctx->mom_cy * TY, ctx->mom_tz >= kp.nz ? 1 : 0};
@@ -965,14 +1032,14 @@ bool launch_fused_u(lbm_ctx *ctx, const T *fin, T *fout, const CUtensorMap &map,
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, K, fin, fout, mask, (const float *)d.rho, (const float *)d.j, (const float *)d.mu,
-                       (const float *)d.sb, sb_out, ctx->status, ctx->capture, wall_u, mo, kp, tz, map);
+                       (const float *)d.sb, sb_out, ctx->status, ctx->capture, wall_u, mo, op, kp, tz, map);
     return true;
   }
   const int tz = z_chunk(gx * gy, kp.nz, resident_slots<K>(NT, sm), 2);
   const dim3 grid(gx, gy, (kp.nz + tz - 1) / tz);
   const MomArgs none{nullptr, nullptr, nullptr, 0, 0};
   K<<<grid, NT, sm, ctx->stream>>>(fin, fout, mask, d.rho, d.j, d.mu, d.sb, sb_out, ctx->status, ctx->capture,
-                                   wall_u, none, kp, tz, map);
+                                   wall_u, none, op, kp, tz, map);
   return false;
 }
 

@@ -7,7 +7,9 @@ magnitudes up to ~7 (liquid density), so a single step is expected within a
 few 1e-7 relative; the bounds below are the targets of the method's precision
 contract (max relative rho error 1e-5 and |du| <= 1e-6 lattice units for FP32
 storage; 1e-3 relative rho for FP16 storage) unless a tighter per-step bound
-is stated.
+is stated.  Where a case's own FP32 rounding floor (the FP64 oracle's
+response to per-step FP32-sized noise, golden/fp32_floor.json) is above
+4e-6, its 50-step density bound is 2.5 times that floor instead.
 """
 import json
 import os
@@ -90,12 +92,20 @@ def test_one_step_from_nonequilibrium_state(name):
     assert absd(got, ref) / scale < 2e-6
 
 
-# Conditioning: FP32-sized noise (6e-8 relative) in the initial state grows
-# in the FP64 oracle itself, after 50 steps, to ~2e-6 relative density for
-# wall_neutral_rates_noq4 (no fourth-order correction, curved interface: the
-# setting Sec. III B reports as unstable) and to <= 8e-7 for the other cases.
-# The bound for that case is scaled by the same factor.
-RHO_TOL_50 = {"wall_neutral_rates_noq4": 5e-5}
+# Conditioning: with FP32-sized noise (6e-8 relative) added to every
+# population after every step, the FP64 oracle itself departs from its clean
+# run after 50 steps by the floor in golden/fp32_floor.json (written by
+# golden/make_fp32_floor.py from the oracle alone): 1.2e-6 - 3.8e-6 relative
+# density for most cases, 5.3e-6 for wall_neutral_rates_noq4 (no
+# fourth-order correction, curved interface) and 1.2e-5 for the general-rate
+# tiles (rates up to 1.6 keep rounding in the higher moments, Eqs. 21-26).
+# An FP32 step rounds at least that much, so each case is held to 1e-5 or
+# 2.5 times its floor, whichever is larger.
+FP32_FLOOR = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fp32_floor.json")))
+
+
+def rho_tol_50(name):
+    return max(1e-5, 2.5 * FP32_FLOOR[name])
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -111,7 +121,7 @@ def test_fifty_steps_from_init(name):
     f = S.run(oracle_init(case), solid, op, 50)
     ref = S.macroscopic(f, solid, op)
     fl = fluid(case)
-    assert rel(m["rho"][fl], ref["rho"][fl]) < RHO_TOL_50.get(name, 1e-5)
+    assert rel(m["rho"][fl], ref["rho"][fl]) < rho_tol_50(name)
     assert absd(m["u"], ref["u"]) < 1e-6
     assert m["mass"] == pytest.approx(float(ref["mass"]), rel=1e-6)
 
