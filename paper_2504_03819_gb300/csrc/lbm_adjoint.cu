@@ -155,6 +155,37 @@ __device__ __forceinline__ void to_central_vjp(float lam[27], const float f[27],
   }
 }
 
+// to_central_vjp when every rate but omega_1 is 1: the collision then reads
+// only k000 and the six second-order central moments (its transpose leaves
+// every other entry of lam exactly zero), and the transpose of the transform
+// has a closed form per population.  With X = c_x - u_x, Y, Z likewise,
+//   lam_q = l000 + l200 X^2 + l020 Y^2 + l002 Z^2 + l110 X Y + l101 X Z + l011 Y Z,
+// and since d k200 / d u_x = -2 k100, d k110 / d u_x = -k010, ..., the
+// u-derivatives need only the first central moments k of the recompute.
+__device__ __forceinline__ void to_central_vjp_unit(float lam[27], const float k[27], float ux, float uy, float uz,
+                                                    float &gux, float &guy, float &guz) {
+  const float l000 = lam[0], l200 = lam[2], l020 = lam[6], l002 = lam[18];
+  const float l110 = lam[4], l101 = lam[10], l011 = lam[12];
+  const float k100 = k[1], k010 = k[3], k001 = k[9];
+  gux += -2.0f * l200 * k100 - l110 * k010 - l101 * k001;
+  guy += -2.0f * l020 * k010 - l110 * k100 - l011 * k001;
+  guz += -2.0f * l002 * k001 - l101 * k100 - l011 * k010;
+  float X[3], Y[3], Z[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    X[c] = (float)(c - 1) - ux;
+    Y[c] = (float)(c - 1) - uy;
+    Z[c] = (float)(c - 1) - uz;
+  }
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int i = q % 3, j = (q / 3) % 3, m = q / 9;
+    const float ax = fmaf(l200, X[i], fmaf(l110, Y[j], l101 * Z[m]));  // multiplies X
+    const float ay = fmaf(l020, Y[j], l011 * Z[m]);                     // multiplies Y
+    lam[q] = fmaf(ax, X[i], fmaf(ay, Y[j], fmaf(l002 * Z[m], Z[m], l000)));
+  }
+}
+
 #define LK(a, b, c) lk[(a) + 3 * (b) + 9 * (c)]
 #define LS(a, b, c) ls[(a) + 3 * (b) + 9 * (c)]
 
@@ -284,6 +315,14 @@ __device__ __forceinline__ void collide_vjp(const float *k, float *ls, float *lk
   gom[10] += (-KM(2, 2, 2) + pm * cs2 * cs2) * LS(2, 2, 2);
 }
 
+// every rate but omega_1 equal to 1 (each 1 - omega_i exactly 0): the rate
+// setting for which the forward step takes its unit-rate collision
+bool adj_unit_rates(const KParams &kp) {
+  for (int i = 0; i < 11; ++i)
+    if (i != 1 && kp.om_c[i] != 0.0f) return false;
+  return true;
+}
+
 // A node of a 3-D launch: blocks of 32 x blockDim.y threads over (x, y), one
 // z-plane per block row of the grid; neighbour indices by periodic offsets.
 struct Site {
@@ -385,8 +424,10 @@ __device__ void block_partials_f64(double (&v)[NPAR], double *partial) {
 // four blocks per SM for FP32 storage (128 registers: about 200 bytes per
 // thread spill to L1, and the extra warps hide more of the kernel's load
 // latency than the spills cost: 1.5% faster than three blocks without
-// spills); the FP16 conversions need the register budget of two
-template <typename T>
+// spills); the FP16 conversions need the register budget of two.  UNIT:
+// every rate but omega_1 is 1 (to_central_vjp_unit; the populations are
+// loaded once).
+template <typename T, bool UNIT>
 __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 4 : 2) k_adj_collide(const T *__restrict__ fstate, const float *__restrict__ sb,
                                                      const uint8_t *__restrict__ mask, const uint32_t *__restrict__ nbr,
                                                      const float *__restrict__ lam_next, float *__restrict__ lam_t,
@@ -461,9 +502,13 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 4 : 2) k_adj_collide(con
 #pragma unroll
       for (int i = 0; i < 11; ++i) gom[i] = 0.0f;
       collide_vjp(k, lam, lk, pm, Fx, Fy, Fz, Qx, Qy, Qz, om1, kp, lpm, lFx, lFy, lFz, lQx, lQy, lQz, lom1, gom);
-      float f[27];  // populations reloaded (L2) rather than kept live
-      load_f(f);
-      to_central_vjp(lk, f, ux, uy, uz, gux, guy, guz);
+      if (UNIT) {
+        to_central_vjp_unit(lk, k, ux, uy, uz, gux, guy, guz);
+      } else {
+        float f[27];  // populations reloaded (L2) rather than kept live
+        load_f(f);
+        to_central_vjp(lk, f, ux, uy, uz, gux, guy, guz);
+      }
 #pragma unroll
       for (int q = 0; q < 27; ++q) lam_t[q * N + n] = lk[q];
       a.u[n] = gux;
@@ -1002,12 +1047,25 @@ void launch_adjoint_step(lbm_ctx *ctx, const void *f_state, const float *lam_nex
   } else {
     launch_fields_full(ctx);  // forward recompute of the fields of f(t) (the state is in ctx->f[cur])
   }
-  if (ctx->storage == LBM_F16)
-    k_adj_collide<__half><<<g4, b4, 0, s>>>((const __half *)f_state, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d,
-                                           ctx->adj, ctx->mask ? ctx->wall_u : nullptr, R.collide, kp);
-  else
-    k_adj_collide<float><<<g4, b4, 0, s>>>((const float *)f_state, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d,
-                                          ctx->adj, ctx->mask ? ctx->wall_u : nullptr, R.collide, kp);
+  const float *wu = ctx->mask ? ctx->wall_u : nullptr;
+  const bool unit = adj_unit_rates(kp);
+  if (ctx->storage == LBM_F16) {
+    const __half *fs = (const __half *)f_state;
+    if (unit)
+      k_adj_collide<__half, true><<<g4, b4, 0, s>>>(fs, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d, ctx->adj, wu,
+                                                    R.collide, kp);
+    else
+      k_adj_collide<__half, false><<<g4, b4, 0, s>>>(fs, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d, ctx->adj, wu,
+                                                     R.collide, kp);
+  } else {
+    const float *fs = (const float *)f_state;
+    if (unit)
+      k_adj_collide<float, true><<<g4, b4, 0, s>>>(fs, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d, ctx->adj, wu,
+                                                   R.collide, kp);
+    else
+      k_adj_collide<float, false><<<g4, b4, 0, s>>>(fs, sb, ctx->mask, ctx->nbr, lam_next, lam_t, d, ctx->adj, wu,
+                                                    R.collide, kp);
+  }
   k_adj_fields<<<g8, b8, 0, s>>>(ctx->mask, d, ctx->adj, kp);
   ctx->launches += 2;
   const float *lmu = adj_mu(ctx);
