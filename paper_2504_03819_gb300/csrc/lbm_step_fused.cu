@@ -557,12 +557,12 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   qpartials(z0, qdummy[0], qdummy[1], qdummy[2]);
   // ring slots of planes z, z+1, z+2 (mu') and z-1, z, z+1 (shift),
   // carried from plane to plane instead of recomputed (no division)
-  int i5a = r4(z0), i5b = r4(z0 + 1), i5c = r4(z0 + 2);
+  int i4a = r4(z0), i4b = r4(z0 + 1), i4c = r4(z0 + 2);
   int i3m = r3(z0 - 1), i3a = r3(z0), i3b = r3(z0 + 1);
   auto advance = [&]() {
-    i5a = i5b;
-    i5b = i5c;
-    i5c = (i5c + 1) & 3;
+    i4a = i4b;
+    i4b = i4c;
+    i4c = (i4c + 1) & 3;
     const int t = i3m;
     i3m = i3a;
     i3a = i3b;
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
     const float ux = uF[t], uy = uF[NT + t], uz = uF[2 * NT + t];
     const float Fx = uF[3 * NT + t], Fy = uF[4 * NT + t], Fz = uF[5 * NT + t];
     const float r_own = S.rho[r4(z)][c1];
-    const float mu_own = S.mu[i5a][(ty + 2) * H2X + tx + 2];
+    const float mu_own = S.mu[i4a][(ty + 2) * H2X + tx + 2];
     if (cap) {  // fields of this state for the adjoint: rho, mu', u, F, Q
       cap[n] = r_own;
       cap[N + n] = mu_own;
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
   for (int z = z0; z < z1; ++z, advance()) {
     if (!dead) {
       // publish mu'(z+2), rho/j(z+1); prefetch mu'(z+3), rho/j(z+2)
-      store(i5c, z + 1);
+      store(i4c, z + 1);
       if (z + 1 < z1) fetch(z + 3, z + 2);
       // populations of this node
       const int n = x + nx * y + nxy * z;
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
         __syncthreads();
       }
       if (!dead) {
-        fields(z + 1, true, i5b, i5c, i3b);
+        fields(z + 1, true, i4b, i4c, i3b);
         __syncthreads();
         // Q of plane z from the partial sums of planes z-1, z (kept) and
         // z+1 (formed now, into the slot of z-1)
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(NT, LBM_FUSED_MINB)
           update(z, n, f, rb, cb, Qx, Qy, Qz);
         } else if (cap && inside) {  // solid node: its wetting rho and mu', no flow
           cap[n] = S.rho[r4(z)][c1];
-          cap[N + n] = S.mu[i5a][(ty + 2) * H2X + tx + 2];
+          cap[N + n] = S.mu[i4a][(ty + 2) * H2X + tx + 2];
 #pragma unroll
           for (int c = 0; c < 9; ++c) cap[(2 + c) * N + n] = 0.0f;
         }
