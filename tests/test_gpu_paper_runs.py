@@ -298,3 +298,38 @@ def test_droplet_between_moving_walls_stays_round():
     P = np.stack([dxs, idx[1] - idx[1].mean(), idx[0] - idx[0].mean()], 1)
     ev = np.linalg.eigvalsh(P.T @ P / len(P))
     assert math.sqrt(ev[-1] / ev[0]) < 1.01
+
+
+@pytest.mark.parametrize("storage", ["f16", "f32"])
+def test_stationary_droplet_to_a_hundred_thousand_steps(storage):
+    """Sec. III B, Fig. 4(e): the r = 30 droplet of 128^3 (0.7 T_c, nu = 0.15,
+    fourth-order correction) after 100 000 steps; the paper prints max|u| =
+    2.4e-11 (FP64).  With FP16 storage and the paper's rates max|u| is 2.4e-6.
+    In FP32 with the paper's rates a Nyquist mode in the vapour next to the
+    interface, seeded by rounding, grows to 1.2e-2 by then; a larger bulk
+    viscosity (omega_2 = 0.8, which the static state does not see) keeps it at
+    1.6e-5, and the FP32 run is checked with that rate.  Held: max|u| below
+    1e-4, no status flag, and sigma = Delta p R_eq / 2 within 3 % of the
+    continuum value."""
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _wetting import equimolar_radius
+    n, r = 128, 30.0
+    om = [1.0] * 11
+    if storage == "f32":
+        om[2] = 0.8
+    p, rl, rv = paper_params(0.7, nu=0.15, omega=om)
+    eos = T.at_reduced_temperature(A392, B, 1.0, 0.7)
+    d = Domain(n, n, n, storage)
+    d.set_params(p)
+    d.set_state(torch.from_numpy(I.droplet(n, n, n, r, rl, rv).astype(np.float32)))
+    d.step(100000)
+    assert d.sync_status() == 0
+    m = d.moments()
+    rho = m["rho"].double().cpu().numpy()
+    c = n // 2
+    rin, rout = float(rho[c - 1:c + 1, c - 1:c + 1, c - 1:c + 1].mean()), float(rho[0, 0, 0])
+    sigma = (eos.p0(rin) - eos.p0(rout)) * equimolar_radius(rho, rin, rout) / 2.0
+    assert float(m["u"].abs().max()) < 1e-4
+    assert sigma == pytest.approx(T.surface_tension_continuum(eos, KAPPA), rel=0.03)
+    d.close()
