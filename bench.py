@@ -440,7 +440,8 @@ def wetting_table(local, steps: int = 10000, iters: int = 9):
 PAPER_WETTING_SETUP = ("Sec. III C runs: 128x256x256, solid planes z=0 and z=255, drop r=30 (tanh width 5) on the "
                        "wall plane z=0.5, vdW a=9/392 b=2/21 T=0.7Tc kappa=0.02, nu=0.15, omega_3=0.5 (with "
                        "omega_3=1 the vapour at the walls grows a mode), other rates 1; angle from a sphere fit to the "
-                       "mid-density surface; start: hemisphere unless a cap angle is given")
+                       "mid-density surface (angle_deg) and from the cap height and base radius (cap_angle_deg); "
+                       "start: hemisphere unless a cap angle is given")
 
 
 def paper_wetting(local):
@@ -455,7 +456,7 @@ def paper_wetting(local):
     from paper_2504_03819_gb300 import Domain, Params
     from paper_2504_03819_gb300 import inputs as I
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from _wetting import contact_angle
+    from _wetting import cap_angle, contact_angle
     nx, ny, nz, r = 128, 256, 256, 30.0
     eos = T.at_reduced_temperature(9.0 / 392.0, 2.0 / 21.0, 1.0, 0.7)
     rl, rv = T.maxwell(eos)
@@ -489,6 +490,7 @@ def paper_wetting(local):
             liquid = rho > 0.5 * (rl + rv)
             on_wall = int(liquid[1].sum())
             out.append({"steps": c, "angle_deg": round(contact_angle(rho, rl, rv, solid), 2) if on_wall else None,
+                        "cap_angle_deg": round(cap_angle(rho, rl, rv), 2) if on_wall else None,
                         "liquid_nodes_on_wall": on_wall,
                         "volume_ratio": round(float(((rho - rv) / (rl - rv))[~solid].sum()) / vol0, 4)})
         d.close()

@@ -8,7 +8,10 @@ and z, linearly interpolated, excluding the first fluid layer above the
 wall; an algebraic least-squares sphere |p - c|^2 = R^2 through them; the
 wall plane z = z_wall (halfway between the solid layer and the first fluid
 layer); the angle inside the liquid from the cap geometry,
-cos(theta) = (z_wall - c_z) / R.
+cos(theta) = (z_wall - c_z) / R.  A second measure (cap_angle) takes the
+drop's height and base radius, tan(theta/2) = h / r_base; on a true
+spherical cap the two agree to a few degrees, so a larger gap between them
+shows a drop whose shape near the wall departs from a cap.
 """
 from __future__ import annotations
 
@@ -54,6 +57,25 @@ def contact_angle(rho: np.ndarray, rho_l: float, rho_v: float, solid: np.ndarray
     P = crossing_points(rho, 0.5 * (rho_l + rho_v), solid, zmin)
     c, R = sphere_fit(P)
     return math.degrees(math.acos(max(-1.0, min(1.0, (z_wall - c[2]) / R))))
+
+
+def cap_angle(rho: np.ndarray, rho_l: float, rho_v: float, z_wall: float = 0.5) -> float:
+    """Contact angle (degrees) from the cap geometry tan(theta/2) = h / r_base:
+    h is the height above the wall plane where the mid-density surface
+    crosses the vertical line through the x-y centre of the domain (linear
+    interpolation between nodes), r_base the radius of a disc with the
+    liquid fraction (rho - rho_v)/(rho_l - rho_v), clipped to [0, 1], of the
+    first fluid layer (z = 1) as its area."""
+    nz, ny, nx = rho.shape
+    mid = 0.5 * (rho_l + rho_v)
+    col = rho[:, ny // 2, nx // 2]
+    h = float("nan")
+    for z in range(1, nz - 2):
+        if col[z] >= mid > col[z + 1]:
+            h = z + (col[z] - mid) / (col[z] - col[z + 1]) - z_wall
+            break
+    area = float(((rho[1] - rho_v) / (rho_l - rho_v)).clip(0.0, 1.0).sum())
+    return math.degrees(2.0 * math.atan2(h, math.sqrt(area / math.pi)))
 
 
 def equimolar_radius(rho: np.ndarray, rho_in: float, rho_out: float) -> float:
