@@ -380,3 +380,39 @@ def test_moving_wall_term_is_the_equilibrium_odd_part():
         d = L.f_eq_phase_space(r, u, m_).reshape(27) - L.f_eq_phase_space(r, -u, m_).reshape(27)
         got = torch.stack([S.wall_odd_equilibrium(i, r, m_, u) for i in range(27)])
         assert float((got - d).abs().max()) < 1e-9 * float(d.abs().max())
+
+
+# ---------------------------------------------------------------------------
+# dependency cone (the basis of the sampled full-size GPU checks)
+# ---------------------------------------------------------------------------
+def test_dependency_cone_of_the_step():
+    """A step moves information at most four nodes: the population arriving
+    at x left x - c_q, whose collision reads Q (phi one node out), u and F
+    there (grad mu two nodes out) and mu (the Laplacian of rho three nodes
+    out).  So after s steps a periodic sub-box of half-width R, cut from the
+    state and stepped alone, agrees with the whole domain within R - 4s of
+    its centre for the densities, and within R - 4s - 2 for the velocity
+    (its force reads mu one node and rho two nodes further).  The full-size
+    GPU checks rest on this; here both sides are the oracle."""
+    n, s, R = 24, 2, 10
+    p, _, _ = params(omega=[1.0, 1.6] + [1.0] * 9)
+    solid = torch.zeros(n, n, n, dtype=torch.bool)
+    f = noneq_state(n, n, n, p, solid, seed=11)
+    full = S.macroscopic(S.run(f, solid, p, s), solid, p)
+    c = (15, 12, 9)  # (x, y, z), off the droplet's centre: the box holds its interface
+    idx = [torch.arange(v - R, v + R + 1) % n for v in c]
+    box = f[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+    sub = S.macroscopic(S.run(box, torch.zeros(box.shape[1:], dtype=torch.bool), p, s),
+                        torch.zeros(box.shape[1:], dtype=torch.bool), p)
+
+    def centre(a, r, boxed):
+        if boxed:
+            k = slice(R - r, R + r + 1)
+            return a[..., k, k, k]
+        return a[..., c[2] - r:c[2] + r + 1, c[1] - r:c[1] + r + 1, c[0] - r:c[0] + r + 1]
+
+    rr, ru = R - 4 * s, R - 4 * s - 2
+    assert float((centre(full["rho"], rr, False) - centre(sub["rho"], rr, True)).abs().max()) < 1e-12
+    assert float((centre(full["u"], ru, False) - centre(sub["u"], ru, True)).abs().max()) < 1e-14
+    # one node further the periodic wrap of the box has arrived
+    assert float((centre(full["u"], ru + 1, False) - centre(sub["u"], ru + 1, True)).abs().max()) > 1e-12
