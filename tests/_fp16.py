@@ -26,6 +26,26 @@ def _shift_classes():
     return L.weights().double().view(27, 1, 1, 1), E.view(27, 1, 1, 1)
 
 
+def rounded_run(f0: torch.Tensor, solid: torch.Tensor, op: S.Params, nsteps: int) -> torch.Tensor:
+    """The oracle's nsteps steps from f0 with every stored population rounded
+    as FP16 storage rounds it (the initial state included)."""
+    w, E = _shift_classes()
+
+    def basis(f):
+        m = S.macroscopic(f, solid, op)
+        return m["rho"], (1.0 + m["mu"] - m["rho"]) / 3.0
+
+    def stored(f, rb, cb):
+        s = w * rb + cb * E
+        return torch.where(solid, f, (f - s).half().double() + s)
+
+    fr = stored(f0, *basis(f0))
+    for _ in range(nsteps):
+        b = basis(fr)
+        fr = stored(S.step(fr, solid, op), *b)
+    return fr
+
+
 @functools.lru_cache(maxsize=None)
 def storage_rounding_error(name: str, nsteps: int) -> float:
     """Max relative fluid density difference between the FP64 oracle with

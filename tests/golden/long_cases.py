@@ -20,6 +20,18 @@ the workload's model parameters and shrinks the domain so the oracle finishes
               oracle itself moves by 1e-3 under 1e-6 noise per step) and goes
               non-finite within 40 000 steps.
 
+The same three at the sizes of the workloads' own parity-run copies:
+
+  droplet64   stationary droplet: 64^3 periodic, R = 8, width 5, u = 0
+  moving64    moving droplet: 64^3 periodic, R = 8 (the 256^3 drop scaled by
+              1/4), width 2, U = (0.05, 0.02, 0), omega_1 = 1.6
+  wall64p     droplet on a wall: 64 x 64 x 32 with solid planes z = 0 and
+              z = 31, hemisphere R = 10, width 5, phi = 1.2, paper EOS
+              coefficient and kappa at 0.8 T_c (as wall32p)
+
+Their results are stored on every fourth z-plane ("planes"), with the fluid
+mass of the whole domain, to keep the files small.
+
 Unless a case sets its own: van der Waals a = 9/49, b = 2/21, R = 1 at T =
 0.85 T_c, kappa = 0.01.
 """
@@ -33,6 +45,13 @@ LONG_CASES = {
                      omega1=1.6, wetting_mode=0, wetting_value=0.0),
     "wall32p": dict(n=(32, 32, 20), radius=8.0, width=5.0, u=(0.0, 0.0, 0.0), walls=(0, 19),
                     omega1=1.0, wetting_mode=1, wetting_value=1.2,
+                    eos=dict(a=9.0 / 392.0, b=2.0 / 21.0, R=1.0, t_over_tc=0.8, kappa=0.02)),
+    "droplet64": dict(n=(64, 64, 64), radius=8.0, width=5.0, u=(0.0, 0.0, 0.0), walls=(),
+                      omega1=1.0, wetting_mode=0, wetting_value=0.0, planes=tuple(range(3, 64, 4))),
+    "moving64": dict(n=(64, 64, 64), radius=8.0, width=2.0, u=(0.05, 0.02, 0.0), walls=(),
+                     omega1=1.6, wetting_mode=0, wetting_value=0.0, planes=tuple(range(3, 64, 4))),
+    "wall64p": dict(n=(64, 64, 32), radius=10.0, width=5.0, u=(0.0, 0.0, 0.0), walls=(0, 31),
+                    omega1=1.0, wetting_mode=1, wetting_value=1.2, planes=tuple(range(1, 32, 4)),
                     eos=dict(a=9.0 / 392.0, b=2.0 / 21.0, R=1.0, t_over_tc=0.8, kappa=0.02)),
 }
 EOS = dict(a=9.0 / 49.0, b=2.0 / 21.0, R=1.0, t_over_tc=0.85, kappa=0.01)

@@ -11,7 +11,11 @@ stage), so the oracle steps a periodic sub-box of half-width R around each
 sampled node, cut from the same input, and its centre must equal the GPU's
 value.  Samples include tile edges and corners of the column tiles and the
 first and last planes of the z chunks of the fused kernel (8 to 32 planes).
+The same bound over several steps gives a multi-step check: after s steps a
+periodic sub-box of half-width R is exact within R - 4s of its centre.
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -114,3 +118,59 @@ def test_wall_256x256x128_sampled():
             (40, 30, nz - 3)]
     check_sampled(d, f, solid, p, pts, R=7, tol=2e-6)
     d.close()
+
+
+# five steps of the 256^3 workload in one sub-box: half-width 30 around
+# (160, 128, 128), exact within 30 - 4 * 5 = 10 after the steps and within 8
+# for the velocity (its force term reads mu one node and rho two nodes out)
+CONE = dict(centre=(160, 128, 128), steps=5, R=30, r=8)
+
+
+@functools.lru_cache(maxsize=None)
+def moving_droplet_256_cone():
+    """Seeded 256^3 state of the moving-droplet workload and the oracle's
+    fields after CONE["steps"] steps on the centre of its sub-box."""
+    n = 256
+    om = [1.0] * 11
+    om[1] = 1.6
+    p = vdw(omega=om)
+    f = seeded_state(I.droplet(n, n, n, 32.0, p.rho_l, p.rho_v, width=2.0), seed=2024)
+    x, y, z = CONE["centre"]
+    R, r = CONE["R"], CONE["r"]
+    fs = sub_box(f, x, y, z, R).double()
+    solid = torch.zeros(fs.shape[1:], dtype=torch.bool)
+    op = oracle_params(p)
+    m = S.macroscopic(S.run(fs, solid, op, CONE["steps"]), solid, op)
+    c = slice(R - r, R + r + 1)
+    return p, f, m["rho"][c, c, c], m["u"][:, c, c, c]
+
+
+@pytest.mark.parametrize("storage,rho_tol,u_tol", [("f32", 1e-5, 1e-6), ("f16", 1e-3, None)])
+def test_moving_droplet_256_five_steps_in_a_cone(storage, rho_tol, u_tol):
+    """The 256^3 moving-droplet workload (a = 9/49, kappa = 0.01, 0.85 T_c,
+    omega_1 = 1.6) from a seeded non-equilibrium state, five steps in the
+    bench's launch configuration, against the FP64 oracle on a 17^3 block
+    around (160, 128, 128): it holds the droplet's interface (x = 159.5), the
+    column-tile edge x = 160, tile rows y = 124, 128 and 132 and the z-chunk
+    boundary z = 128 of the fused kernel.  Density and velocity at the
+    method's precision contract (FP32 storage: relative density 1e-5, |du|
+    1e-6; FP16 storage: relative density 1e-3)."""
+    p, f, ref_rho, ref_u = moving_droplet_256_cone()
+    n = 256
+    d = Domain(n, n, n, storage)
+    d.set_params(p)
+    d.set_populations(f)
+    d.step(CONE["steps"])
+    assert d.sync_status() == 0
+    m = d.moments()
+    d.close()
+    (x, y, z), r = CONE["centre"], CONE["r"]
+    sx, sy, sz = slice(x - r, x + r + 1), slice(y - r, y + r + 1), slice(z - r, z + r + 1)
+    rho = m["rho"][sz, sy, sx].double().cpu()
+    u = m["u"][:, sz, sy, sx].double().cpu()
+    e_rho = float(((rho - ref_rho).abs() / ref_rho.abs()).max())
+    e_u = float((u - ref_u).abs().max())
+    print(f"256^3 cone, {storage}: rel rho {e_rho:.3e}, |du| {e_u:.3e}")
+    assert e_rho < rho_tol
+    if u_tol is not None:
+        assert e_u < u_tol
