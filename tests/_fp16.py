@@ -53,22 +53,10 @@ def storage_rounding_error(name: str, nsteps: int) -> float:
     case = build(name)
     solid = torch.from_numpy(case["mask"].astype(bool))
     op = oracle_params(case["p"])
-    w, E = _shift_classes()
-
-    def basis(f):
-        m = S.macroscopic(f, solid, op)
-        return m["rho"], (1.0 + m["mu"] - m["rho"]) / 3.0
-
-    def stored(f, rb, cb):
-        s = w * rb + cb * E
-        return torch.where(solid, f, (f - s).half().double() + s)
-
     f0 = oracle_init(case)
-    fr = stored(f0, *basis(f0))
+    fr = rounded_run(f0, solid, op, nsteps)
     fx = f0
     for _ in range(nsteps):
-        b = basis(fr)
-        fr = stored(S.step(fr, solid, op), *b)
         fx = S.step(fx, solid, op)
     r, x = S.macroscopic(fr, solid, op)["rho"], S.macroscopic(fx, solid, op)["rho"]
     fl = ~solid
